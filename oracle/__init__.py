@@ -1,0 +1,159 @@
+"""FP64 CPU oracle for the miniBUDE pose energy (arxiv 2509.21039, Sec. 3,
+Listing 4, Eq. 3) -- TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never calls it and
+has no fallback to it.  The arithmetic lives in ``bude_oracle.c`` (plain C,
+double precision, a triple loop over poses, ligand atoms and protein atoms);
+this module only compiles it with gcc and marshals numpy arrays through
+ctypes.  The pair energy it evaluates is the project's own definition (the
+paper never writes the forcefield down); ``bude_oracle.c`` states it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bude_oracle.c")
+_LIB = os.path.join(_HERE, "libbude_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# gcc flags: no fast-math, no contraction, no target-specific flags, so x86
+# and Arm hosts round identically.
+_CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+           "-shared", "-std=c11"]
+
+
+def build(force: bool = False) -> str:
+    """Compile ``bude_oracle.c`` into ``libbude_oracle.so`` (gcc, OpenMP)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", *_CFLAGS, _SRC, "-o", tmp, "-lm"], check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int32)
+        i64 = ctypes.c_int64
+        ci = ctypes.c_int
+        cd = ctypes.c_double
+        lib.oracle_pair_energy.restype = cd
+        lib.oracle_pair_energy.argtypes = [cd, cd, cd, ci, cd, cd, cd, ci, cd]
+        lib.oracle_pair_denergy.restype = cd
+        lib.oracle_pair_denergy.argtypes = [cd, cd, cd, ci, cd, cd, cd, ci, cd]
+        lib.oracle_rotation.restype = None
+        lib.oracle_rotation.argtypes = [cd, cd, cd, dp]
+        deck_args = [ci, dp, ip, ci, dp, ip, ci, dp, dp, dp, ip]
+        lib.oracle_energies.restype = ci
+        lib.oracle_energies.argtypes = deck_args + [i64, dp, dp, dp, ci]
+        lib.oracle_pose_grad.restype = ci
+        lib.oracle_pose_grad.argtypes = deck_args + [i64, dp, dp, dp, ci]
+        lib.oracle_max_threads.restype = ci
+        lib.oracle_max_threads.argtypes = []
+        _lib = lib
+        return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _iptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def max_threads() -> int:
+    """OpenMP threads the oracle uses when asked for all cores."""
+    return int(_load().oracle_max_threads())
+
+
+def pair_energy(ff_a, ff_b, d: float) -> float:
+    """e(a, b, d) for per-type rows ``(radius, hardness, elsc, hbtype)``."""
+    ra, ha, qa, hba = ff_a
+    rb, hb, qb, hbb = ff_b
+    return float(_load().oracle_pair_energy(ra, ha, qa, int(hba), rb, hb, qb,
+                                            int(hbb), float(d)))
+
+
+def pair_denergy(ff_a, ff_b, d: float) -> float:
+    """de/dd for per-type rows ``(radius, hardness, elsc, hbtype)``."""
+    ra, ha, qa, hba = ff_a
+    rb, hb, qb, hbb = ff_b
+    return float(_load().oracle_pair_denergy(ra, ha, qa, int(hba), rb, hb, qb,
+                                             int(hbb), float(d)))
+
+
+def rotation(a0: float, a1: float, a2: float) -> np.ndarray:
+    """R = Rz(a2) Ry(a1) Rx(a0) as a 3x3 float64 array."""
+    out = np.zeros(9, np.float64)
+    _load().oracle_rotation(float(a0), float(a1), float(a2), _dptr(out))
+    return out.reshape(3, 3)
+
+
+def _deck_args(deck):
+    lig = np.ascontiguousarray(deck["lig_xyz"], np.float64).reshape(-1, 3)
+    pro = np.ascontiguousarray(deck["pro_xyz"], np.float64).reshape(-1, 3)
+    lt = np.ascontiguousarray(deck["lig_type"], np.int32)
+    pt = np.ascontiguousarray(deck["pro_type"], np.int32)
+    rad = np.ascontiguousarray(deck["radius"], np.float64)
+    hard = np.ascontiguousarray(deck["hardness"], np.float64)
+    elsc = np.ascontiguousarray(deck["elsc"], np.float64)
+    hbt = np.ascontiguousarray(deck["hbtype"], np.int32)
+    keep = (lig, pro, lt, pt, rad, hard, elsc, hbt)
+    args = [len(lt), _dptr(lig), _iptr(lt), len(pt), _dptr(pro), _iptr(pt),
+            len(rad), _dptr(rad), _dptr(hard), _dptr(elsc), _iptr(hbt)]
+    return args, keep
+
+
+def energies(deck, poses, n_threads: int = 0, with_abs: bool = False):
+    """Per-pose energies (float64) of ``poses`` ([6][n]) on ``deck``.
+
+    ``deck`` is a mapping with lig_xyz, lig_type, pro_xyz, pro_type, radius,
+    hardness, elsc, hbtype.  ``n_threads`` 0 runs one thread, -1 all cores.
+    With ``with_abs`` also returns 0.5 * sum |e| per pose (the error scale).
+    """
+    lib = _load()
+    args, keep = _deck_args(deck)
+    P = np.ascontiguousarray(poses, np.float64).reshape(6, -1)
+    n = P.shape[1]
+    E = np.zeros(n, np.float64)
+    A = np.zeros(n, np.float64)
+    nt = lib.oracle_max_threads() if n_threads < 0 else n_threads
+    rc = lib.oracle_energies(*args, n, _dptr(P), _dptr(E), _dptr(A), nt)
+    del keep
+    if rc != 0:
+        raise ValueError("oracle_energies rejected the deck (type out of range "
+                         "or negative size)")
+    return (E, A) if with_abs else E
+
+
+def pose_grad(deck, poses, n_threads: int = 0):
+    """(energies [n], dE/dpose [6][n]) in float64 from the analytic chain rule."""
+    lib = _load()
+    args, keep = _deck_args(deck)
+    P = np.ascontiguousarray(poses, np.float64).reshape(6, -1)
+    n = P.shape[1]
+    E = np.zeros(n, np.float64)
+    G = np.zeros((6, n), np.float64)
+    nt = lib.oracle_max_threads() if n_threads < 0 else n_threads
+    rc = lib.oracle_pose_grad(*args, n, _dptr(P), _dptr(E), _dptr(G), nt)
+    del keep
+    if rc != 0:
+        raise ValueError("oracle_pose_grad rejected the deck")
+    return E, G
