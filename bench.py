@@ -1,0 +1,344 @@
+"""Throughput of the pose-energy hot path on GB300 (one JSON line on stdout).
+
+A step is one bude_energies call over the full-size synthetic deck: 64
+ligand atoms x 2672 protein atoms x 65536 poses (pose transform, pair loop,
+per-pose reduction, output), inputs resident in HBM.  L2 is flushed (a
+256 MiB write) before every timed step; each step is timed with CUDA events
+on the launching stream.  ``value`` is poses per second over all ranks;
+``e2e`` repeats the step through the public API from pinned host buffers,
+host<->device copies included.  ``roofline`` rates the kernel against the
+FP32 CUDA-core peak (152 SMs x 128 lanes x 2 FLOP x 2.07 GHz); FLOPs per
+step follow Eq. 3 of the paper.  ``cpu_baseline`` times the FP64 oracle on
+a bounded sample of the same workload on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--variant fast]
+  python bench.py --impl reference     # the oracle arm on the host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FULL = dict(n_lig=64, n_pro=2672, n_types=34, n_poses=65536)
+SMALL = dict(n_lig=26, n_pro=938, n_types=34, n_poses=4096)
+METRIC = "pose energies/s"
+SM_MAX_MHZ = 2070.0
+FP32_LANES_PER_SM = 128
+
+
+def eq3_flops(n_lig, n_pro, n_poses, ppwi):
+    """Eq. 3: per work-item 28 P + nlig (2 + 18 P + npro (10 + 30 P)), x poses / P."""
+    per_item = 28 * ppwi + n_lig * (2 + 18 * ppwi + n_pro * (10 + 30 * ppwi))
+    return per_item * (n_poses / ppwi)
+
+
+def algorithmic_flops(n_lig, n_pro, n_poses):
+    """Eq. 3 in its many-poses-per-item limit: 28 + nlig (18 + 30 npro) per pose."""
+    return n_poses * (28 + n_lig * (18 + 30 * n_pro))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0, path=None):
+        self.index = index
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+            if self.path:
+                with open(self.path, "w") as f:
+                    f.write(self.Q + "\n" + "\n".join(self.lines) + "\n")
+
+    def summary(self):
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "power_w_max": max(power) if power else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_leg(deck, n_poses_total, budget_s=12.0, threads=-1):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload's
+    poses (about budget_s of host CPU time).  Returns (poses/s, sample size,
+    seconds, threads, sample energies, sample absolute-term sums)."""
+    import oracle
+    oracle.build()
+    cores = oracle.max_threads() if threads < 0 else threads
+    k = max(cores, 8)
+    t0 = time.perf_counter()
+    oracle.energies(deck, deck["poses"][:, :k], n_threads=threads)
+    dt = time.perf_counter() - t0
+    n = int(min(n_poses_total, max(k, k * budget_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    E, A = oracle.energies(deck, deck["poses"][:, :n], n_threads=threads, with_abs=True)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, cores, E, A
+
+
+def reference_arm(args):
+    """The FP64 oracle as it stands, timed on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2509_21039_gb300 import synth
+    import oracle
+    oracle.build()
+    D = synth.make_deck(1, **FULL)
+    cores = oracle.max_threads()
+    # per step: a bounded sample of the poses, sized so the whole run stays short
+    per_step = max(cores, 16)
+    for _ in range(args.warmup):
+        oracle.energies(D, D["poses"][:, :cores], n_threads=-1)
+    times = []
+    for s in range(args.steps):
+        lo = (s * per_step) % (FULL["n_poses"] - per_step)
+        t0 = time.perf_counter()
+        oracle.energies(D, D["poses"][:, lo:lo + per_step], n_threads=-1)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    val = per_step / (ms / 1e3)
+    sample = f"{per_step} poses per step of the 64x2672x65536 deck, FP64, {cores} threads"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "poses/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "full-size FP32 deck 64 lig x 2672 pro x 65536 poses, seed 1",
+                       "l2": "not applicable (host CPU)"},
+            "cpu_baseline": {"value": val, "unit": "poses/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "poses/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", default="fast", choices=["ieee", "fast", "comp"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the variant table and the batched comparison")
+    ap.add_argument("--small", action="store_true", help="26x938x4096 deck")
+    ap.add_argument("--poses", type=int, default=0, help="override the pose count (profiling)")
+    ap.add_argument("--flush-mb", type=int, default=256, help="L2 flush buffer, MiB")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2509_21039_gb300 import bude, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    shape = dict(SMALL if args.small else FULL)
+    if args.poses:
+        shape["n_poses"] = args.poses
+    # each rank docks its own deck (independent problems: weak scaling)
+    D = synth.make_deck(1 + rank, **shape)
+    deck = bude.Deck(D, device=dev)
+    poses = torch.from_numpy(D["poses"]).to(dev)
+    n = poses.shape[1]
+    out = torch.empty(n, dtype=torch.float32, device=dev)
+    flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    opts = bude.LaunchOptions(variant=args.variant)
+    resolved = bude.default_options(args.variant)
+
+    def step():
+        bude.energies(deck, poses, out=out, opts=opts)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            flush.zero_()
+            fn()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        evs = []
+        launches = 0
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            launches += bude.launch_count()
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        barrier()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return ms, launches
+
+    with ClockSampler(local, os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
+                      if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None) as clk:
+        ms, launches = timed(step, args.steps, args.warmup)
+    ms_mean = statistics.mean(ms)
+    if world > 1:
+        t = torch.tensor([ms_mean], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_mean = float(t.item())
+    value = world * n / (ms_mean / 1e3)
+
+    # end to end through the public API: pinned host poses in, host energies out
+    host_poses = torch.from_numpy(D["poses"]).pin_memory()
+    host_out = torch.empty(n, dtype=torch.float32).pin_memory()
+    dev_poses = torch.empty_like(poses)
+
+    def e2e_step():
+        dev_poses.copy_(host_poses, non_blocking=True)
+        bude.energies(deck, dev_poses, out=out, opts=opts)
+        host_out.copy_(out, non_blocking=True)
+
+    e2e_ms, _ = timed(e2e_step, max(3, args.steps // 2), 2)
+    e2e_mean = statistics.mean(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_mean], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_mean = float(t.item())
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clocks = clk.summary()
+    peak_max = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    alg = algorithmic_flops(shape["n_lig"], shape["n_pro"], n)
+    achieved = alg / (ms_mean / 1e3) / 1e12 / world  # per GPU, per launch
+    ppwi = resolved.ppwi
+    roofline = {
+        "bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
+        "frac": achieved / peak_max, "traffic": None,
+        "kernel": f"pose_kernel<{args.variant}, P={ppwi}>",
+        "flops_per_launch": alg,
+        "flop_count": "Eq. 3 in the many-poses limit: 28 + nlig (18 + 30 npro) per pose",
+        "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz",
+        "eq3_tflops_at_ppwi": eq3_flops(shape["n_lig"], shape["n_pro"], n, ppwi) / (ms_mean / 1e3) / 1e12,
+    }
+    if clocks:
+        clk_peak = sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12
+        roofline["frac_at_measured_clock"] = achieved / clk_peak
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "poses/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mean,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": (f"deck {shape['n_lig']} lig x {shape['n_pro']} pro x "
+                                f"{shape['n_poses']} poses, 34 types, seed 1+rank"),
+                   "variant": args.variant, "ppwi": ppwi, "block": resolved.block,
+                   "ctas_per_sm": resolved.ctas_per_sm,
+                   "l2": f"flushed ({args.flush_mb} MiB write) before every timed step",
+                   "parallelism": f"independent decks per GPU x{world}"},
+        "gpu_launches": int(launches),
+        "e2e": {"value": world * n / (e2e_mean / 1e3), "unit": "poses/s",
+                "h2d_bytes_per_step": int(host_poses.numel() * 4),
+                "d2h_bytes_per_step": int(host_out.numel() * 4)},
+        "roofline": roofline,
+        "clocks": clocks,
+    }
+
+    # CPU-baseline leg: the FP64 oracle on a bounded sample of the same poses.
+    # Its sample energies also give each variant's error on that sample.
+    if not args.no_cpu_baseline:
+        v, k, dt, cores, ref, A = cpu_baseline_leg(D, n)
+        line["cpu_baseline"] = {"value": v, "unit": "poses/s", "cores": cores, "kind": "oracle",
+                                "sample": f"first {k} poses of the same deck, FP64, {dt:.1f} s"}
+        if not args.no_extras:
+            variants = {}
+            for vname in ("ieee", "fast", "comp"):
+                o = bude.LaunchOptions(variant=vname)
+                vms, _ = timed(lambda: bude.energies(deck, poses, out=out, opts=o), 5, 2)
+                E = out[:k].cpu().numpy().astype(np.float64)
+                err = np.abs(E - ref) / np.maximum(A, 1.0)
+                rel = np.abs(E - ref) / np.maximum(np.abs(ref), 1e-30)
+                t = statistics.mean(vms) / 1e3
+                variants[vname] = {"poses_per_s": n / t,
+                                   "frac_fp32_peak": alg / t / 1e12 / peak_max,
+                                   "scaled_err_max": float(err.max()),
+                                   "rel_err_median": float(np.median(rel)),
+                                   "rel_err_max": float(rel.max()),
+                                   "error_sample_poses": int(k)}
+            line["variants"] = variants
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

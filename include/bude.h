@@ -1,0 +1,180 @@
+/*
+ * bude.h -- C ABI of the GB300 (sm_103a) pose-energy library libbude.so.
+ *
+ * The library evaluates the per-pose protein-ligand docking energy that the
+ * miniBUDE "fasten" kernel computes (arxiv 2509.21039, Sec. 3, Listing 4; FLOP
+ * count Eq. 3): every pose moves the ligand rigidly (three angles, three
+ * translations), every ligand x protein atom pair is scored by steric,
+ * electrostatic and desolvation terms looked up by atom-type pair, and half
+ * the sum is the pose energy.  The paper does not write the forcefield down;
+ * the pair energy used here is, with R = r_a + r_b, H = (h_a + h_b)/2,
+ * Q = q_a q_b, s = d - R and phi(u) = clamp-to-[0,1] cubic (1-u)^2 (1+2u):
+ *
+ *   e = H (s/R)^2 [s<0] + 4 Q w phi(s/4) + S phi(s/2)
+ *
+ * where w = 2 for a donor-acceptor pair (else 1) and S = 1/2 when exactly one
+ * atom of the pair is polar (hbtype != 0), else 0.  All terms vanish for
+ * d >= R + 4 Angstrom.
+ *
+ * Conventions shared by every call
+ *  - Pointers named "device" must be CUDA device (or managed) memory of the
+ *    current device; the library never dereferences them on the host.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Compute calls are asynchronous on it and never synchronise,
+ *    except where a call says otherwise.
+ *  - Every call returns BUDE_OK (0) or a negative BUDE_ERR_* code and never
+ *    aborts, asserts or traps.  bude_status_string() names a code;
+ *    bude_last_error() gives a one-line message for the last failure on the
+ *    calling thread.
+ *  - Calls that use the same deck (or the same batch plan) must not overlap
+ *    on the GPU: they share the deck's scratch workspace.
+ */
+#ifndef BUDE_H
+#define BUDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define BUDE_API __attribute__((visibility("default")))
+#else
+#define BUDE_API
+#endif
+
+#define BUDE_OK 0
+#define BUDE_ERR_INVALID_ARG (-1) /* null pointer, bad size, type or option */
+#define BUDE_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define BUDE_ERR_OOM (-3)         /* device allocation failed */
+#define BUDE_ERR_UNSUPPORTED (-4) /* shape or option outside what is built */
+#define BUDE_ERR_DEVICE_FLAG (-5) /* a device-side check raised its error word */
+
+/* Arithmetic variants of the energy kernels. */
+#define BUDE_FP32_IEEE 0 /* FP32, correctly rounded sqrt/div, no flush-to-zero */
+#define BUDE_FP32_FAST 1 /* FP32, approximate sqrt and sin/cos, flush-to-zero */
+#define BUDE_FP32_COMP 2 /* as IEEE, each ligand atom's FP32 sum folded in FP64 */
+#define BUDE_FP64 3      /* every operation in FP64 */
+
+/* Limits of this build. */
+#define BUDE_MAX_TYPES 1024
+
+/*
+ * Deck description: the three inputs of Listing 4 besides the poses.
+ * Atom records are 16 bytes, {x, y, z, type}, the type being an int32 stored
+ * in the fourth 4-byte word (Sec. 3 describes the same flattening of the
+ * Atom struct to four 4-byte fields).  Forcefield rows are
+ * {radius, hardness, elsc, hbtype} with hbtype an int32 in the fourth word
+ * (0 none, 1 donor, 2 acceptor).
+ */
+typedef struct {
+    int32_t n_lig;          /* ligand atoms, >= 0 */
+    int32_t n_pro;          /* protein atoms, >= 0 */
+    int32_t n_types;        /* forcefield rows, 1..BUDE_MAX_TYPES */
+    const float* lig_xyzt;  /* device, [n_lig][4] */
+    const float* pro_xyzt;  /* device, [n_pro][4] */
+    const float* ff;        /* device, [n_types][4] */
+} bude_deck_desc;
+
+/*
+ * Launch options.  Zero in any field selects the library default for the
+ * variant (the defaults come from the autotuner's tables compiled in or set
+ * with bude_set_default_options).
+ */
+typedef struct {
+    int32_t variant;     /* BUDE_FP32_IEEE .. BUDE_FP64 */
+    int32_t ppwi;        /* poses per thread: 1, 2, 4, 8 or 16 (FP64: 1, 2, 4) */
+    int32_t block;       /* threads per CTA: multiple of 32 in [64, 1024] */
+    int32_t tile;        /* protein atoms staged per shared-memory chunk */
+    int32_t ctas_per_sm; /* resident CTAs per SM of the persistent grid */
+} bude_options;
+
+typedef struct bude_deck bude_deck;
+typedef struct bude_batch bude_batch;
+
+/*
+ * bude_create_deck -- validate and repack one deck into buffers it owns.
+ *
+ * Copies desc's device arrays into the deck (the caller may free its own
+ * copies once this call returns), maps each ligand type to a compact row of
+ * the type-pair table and builds the pair parameters of the forcefield's
+ * combination rules on the device (the table lookup of Eq. 3's 10 per-pair
+ * FLOPs).  Runs on "stream" and SYNCHRONISES it to read the validation word.
+ * Errors: BUDE_ERR_INVALID_ARG for null pointers, negative sizes,
+ * n_types outside 1..BUDE_MAX_TYPES, an atom type outside [0, n_types), a
+ * non-finite coordinate, a radius <= 0 or non-finite forcefield value, or an
+ * hbtype outside {0, 1, 2}; BUDE_ERR_UNSUPPORTED when the pair table cannot
+ * fit in shared memory; BUDE_ERR_OOM / BUDE_ERR_CUDA otherwise.  On error
+ * *out is set to NULL.
+ */
+BUDE_API int bude_create_deck(const bude_deck_desc* desc, void* stream, bude_deck** out);
+
+/* Free a deck and its workspace (synchronises the device first). NULL is OK. */
+BUDE_API int bude_destroy_deck(bude_deck* deck);
+
+/* Sizes recorded in a deck (any pointer may be NULL). */
+BUDE_API int bude_deck_info(const bude_deck* deck, int32_t* n_lig, int32_t* n_pro,
+                   int32_t* n_types, int32_t* n_rows);
+
+/*
+ * bude_energies -- energy of n poses (Listing 4, whole kernel).
+ *
+ * poses:    device float32 [6][n]: rows 0..2 are the angles about x, y, z,
+ *           rows 3..5 the translation; the pose rotation is
+ *           R = Rz(a2) Ry(a1) Rx(a0) (first element cos(a1) cos(a2) as in
+ *           Listing 4) applied about the ligand's coordinate origin.
+ * energies: device float32 [n], written as 0.5 * sum of pair energies.
+ * opts:     NULL for defaults.
+ * n = 0 is a no-op.  A deck with no ligand or no protein atoms yields zeros.
+ * A pose whose transform has a NaN yields NaN.  The first call with a larger
+ * n than before grows the deck's workspace with stream-ordered allocation;
+ * make such a call before capturing the stream into a CUDA graph.
+ */
+BUDE_API int bude_energies(bude_deck* deck, const float* poses, int64_t n,
+                  float* energies, const bude_options* opts, void* stream);
+
+/*
+ * bude_energies_batched -- many decks in one persistent launch.
+ *
+ * decks[i], poses[i] (device [6][n[i]]) and energies[i] (device [n[i]]) for
+ * i < count describe independent docking problems of uneven sizes.  All of
+ * them run in one launch of a persistent kernel that splits the combined
+ * (pose tile x ligand atom x protein atom) space evenly over the grid.  The
+ * first call with a given set of arguments builds a plan (work-list
+ * descriptors, workspace) and captures the launch into a CUDA graph; calls
+ * with the same arguments replay that graph.  Results equal bude_energies'
+ * within the variant's rounding (the summation order differs).
+ */
+BUDE_API int bude_energies_batched(bude_deck* const* decks, const float* const* poses,
+                          const int64_t* n, float* const* energies,
+                          int32_t count, const bude_options* opts, void* stream);
+
+/*
+ * bude_pose_grad -- energies and their gradient with respect to the six pose
+ * parameters (the adjoint of bude_energies).
+ *
+ * grad: device float32 [6][n], d energy / d pose row j.  energies may be
+ * NULL.  Variants BUDE_FP32_IEEE and BUDE_FP32_FAST (COMP maps to IEEE with
+ * FP64 folds; FP64 computes in double).  A pair at zero distance adds no
+ * gradient.
+ */
+BUDE_API int bude_pose_grad(bude_deck* deck, const float* poses, int64_t n,
+                   float* energies, float* grad, const bude_options* opts,
+                   void* stream);
+
+/* Default options the library uses for a variant when a field is zero. */
+BUDE_API int bude_get_default_options(int32_t variant, bude_options* out);
+BUDE_API int bude_set_default_options(const bude_options* opts);
+
+/* Kernel launches the last compute call on this thread enqueued. */
+BUDE_API int64_t bude_last_launch_count(void);
+
+BUDE_API const char* bude_status_string(int status);
+BUDE_API const char* bude_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BUDE_H */

@@ -63,7 +63,7 @@ def _load():
         lib.oracle_energies.restype = ci
         lib.oracle_energies.argtypes = deck_args + [i64, dp, dp, dp, ci]
         lib.oracle_pose_grad.restype = ci
-        lib.oracle_pose_grad.argtypes = deck_args + [i64, dp, dp, dp, ci]
+        lib.oracle_pose_grad.argtypes = deck_args + [i64, dp, dp, dp, dp, ci]
         lib.oracle_max_threads.restype = ci
         lib.oracle_max_threads.argtypes = []
         _lib = lib
@@ -143,17 +143,22 @@ def energies(deck, poses, n_threads: int = 0, with_abs: bool = False):
     return (E, A) if with_abs else E
 
 
-def pose_grad(deck, poses, n_threads: int = 0):
-    """(energies [n], dE/dpose [6][n]) in float64 from the analytic chain rule."""
+def pose_grad(deck, poses, n_threads: int = 0, with_scale: bool = False):
+    """(energies [n], dE/dpose [6][n]) in float64 from the analytic chain rule.
+
+    With ``with_scale`` also returns [2][n] error scales: 0.5 sum |e'| |r| for
+    the angle rows and 0.5 sum |e'| for the translation rows.
+    """
     lib = _load()
     args, keep = _deck_args(deck)
     P = np.ascontiguousarray(poses, np.float64).reshape(6, -1)
     n = P.shape[1]
     E = np.zeros(n, np.float64)
     G = np.zeros((6, n), np.float64)
+    S = np.zeros((2, n), np.float64)
     nt = lib.oracle_max_threads() if n_threads < 0 else n_threads
-    rc = lib.oracle_pose_grad(*args, n, _dptr(P), _dptr(E), _dptr(G), nt)
+    rc = lib.oracle_pose_grad(*args, n, _dptr(P), _dptr(E), _dptr(G), _dptr(S), nt)
     del keep
     if rc != 0:
         raise ValueError("oracle_pose_grad rejected the deck")
-    return E, G
+    return (E, G, S) if with_scale else (E, G)

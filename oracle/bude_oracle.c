@@ -256,11 +256,13 @@ static double dot3(const double a[3], const double b[3])
  * dR/da_j x_l is written out from the product R = Rz Ry Rx by differentiating
  * the factor that holds a_j, e.g. dR/da1 = Rz Ry' Rx, so no torque identity is
  * assumed here.  A pair at d = 0 contributes no gradient (direction
- * undefined, and e'(0) (x'-p)/d has no limit).
+ * undefined, and e'(0) (x'-p)/d has no limit).  When scale is not NULL it
+ * receives, per pose, 0.5 sum |e'| |r_l| (a bound on each angle derivative)
+ * and 0.5 sum |e'| (a bound on each translation derivative): [2][n_poses].
  */
 static void grad_range(const oracle_deck* D, int64_t n_poses,
                        const double* poses, int64_t k0, int64_t k1,
-                       double* energy, double* grad)
+                       double* energy, double* grad, double* scale)
 {
     for (int64_t k = k0; k < k1; ++k) {
         double a0 = poses[0 * n_poses + k], a1 = poses[1 * n_poses + k],
@@ -291,13 +293,14 @@ static void grad_range(const oracle_deck* D, int64_t n_poses,
         double t[3] = {poses[3 * n_poses + k], poses[4 * n_poses + k],
                        poses[5 * n_poses + k]};
         double E = 0.0, G[6] = {0, 0, 0, 0, 0, 0};
+        double abs_f = 0.0, abs_t = 0.0; /* error scales: sum |e'|, sum |r| |e'| */
         for (int l = 0; l < D->n_lig; ++l) {
             const double* x = D->lig_xyz + 3 * l;
             double xp[3];
             for (int i = 0; i < 3; ++i)
                 xp[i] = R[3 * i + 0] * x[0] + R[3 * i + 1] * x[1] +
                         R[3 * i + 2] * x[2] + t[i];
-            double g[3] = {0, 0, 0};
+            double g[3] = {0, 0, 0}, abs_l = 0.0;
             for (int p = 0; p < D->n_pro; ++p) {
                 const double* y = D->pro_xyz + 3 * p;
                 double dv[3] = {xp[0] - y[0], xp[1] - y[1], xp[2] - y[2]};
@@ -305,10 +308,15 @@ static void grad_range(const oracle_deck* D, int64_t n_poses,
                 pair_params pp = deck_pair(D, D->lig_type[l], D->pro_type[p]);
                 E += pair_energy_pp(&pp, d);
                 if (d > 0.0) {
-                    double f = pair_denergy_pp(&pp, d) / d;
+                    double de = pair_denergy_pp(&pp, d);
+                    double f = de / d;
                     for (int i = 0; i < 3; ++i) g[i] += f * dv[i];
+                    abs_l += fabs(de);
                 }
             }
+            double r[3] = {xp[0] - t[0], xp[1] - t[1], xp[2] - t[2]};
+            abs_f += abs_l;
+            abs_t += abs_l * sqrt(dot3(r, r));
             /* 0.5 factor of the output applied once at the end */
             double v0[3], v1[3], v2[3];
             for (int i = 0; i < 3; ++i) {
@@ -325,6 +333,10 @@ static void grad_range(const oracle_deck* D, int64_t n_poses,
         }
         if (energy) energy[k] = 0.5 * E;
         for (int j = 0; j < 6; ++j) grad[j * n_poses + k] = 0.5 * G[j];
+        if (scale) {
+            scale[k] = 0.5 * abs_t;           /* bounds |dE/da_j| */
+            scale[n_poses + k] = 0.5 * abs_f; /* bounds |dE/dt_j| */
+        }
     }
 }
 
@@ -333,7 +345,7 @@ int oracle_pose_grad(int n_lig, const double* lig_xyz, const int32_t* lig_type,
                      int n_types, const double* radius, const double* hardness,
                      const double* elsc, const int32_t* hbtype,
                      int64_t n_poses, const double* poses, double* energy,
-                     double* grad, int n_threads)
+                     double* grad, double* scale, int n_threads)
 {
     oracle_deck D = {n_lig, n_pro, n_types, lig_xyz, lig_type, pro_xyz,
                      pro_type, radius, hardness, elsc, hbtype};
@@ -342,12 +354,12 @@ int oracle_pose_grad(int n_lig, const double* lig_xyz, const int32_t* lig_type,
     if (n_threads > 0) {
 #pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
         for (int64_t k = 0; k < n_poses; ++k)
-            grad_range(&D, n_poses, poses, k, k + 1, energy, grad);
+            grad_range(&D, n_poses, poses, k, k + 1, energy, grad, scale);
         return 0;
     }
 #endif
     (void)n_threads;
-    grad_range(&D, n_poses, poses, 0, n_poses, energy, grad);
+    grad_range(&D, n_poses, poses, 0, n_poses, energy, grad, scale);
     return 0;
 }
 

@@ -1,0 +1,307 @@
+"""ctypes binding of libbude.so (C ABI in include/bude.h).
+
+Argument marshalling only: tensors are checked for device, dtype, shape and
+contiguity and their pointers handed to the library, which runs every step
+of the energy evaluation in its own CUDA kernels.  PyTorch supplies device
+memory and streams.  There is no fallback: if ``libbude.so`` is missing or a
+call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libbude.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "bude.h")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_CUDA = -2
+ERR_OOM = -3
+ERR_UNSUPPORTED = -4
+ERR_DEVICE_FLAG = -5
+
+FP32_IEEE = 0
+FP32_FAST = 1
+FP32_COMP = 2
+FP64 = 3
+VARIANTS = {"ieee": FP32_IEEE, "fast": FP32_FAST, "comp": FP32_COMP, "fp64": FP64}
+MAX_TYPES = 1024
+
+
+class BudeError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} ({code})")
+        self.code = code
+
+
+class DeckDesc(ctypes.Structure):
+    _fields_ = [("n_lig", ctypes.c_int32), ("n_pro", ctypes.c_int32),
+                ("n_types", ctypes.c_int32), ("lig_xyzt", ctypes.c_void_p),
+                ("pro_xyzt", ctypes.c_void_p), ("ff", ctypes.c_void_p)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("ppwi", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libbude.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    ci = ctypes.c_int
+    sig = {
+        "bude_create_deck": (ci, [ctypes.POINTER(DeckDesc), vp, ctypes.POINTER(vp)]),
+        "bude_destroy_deck": (ci, [vp]),
+        "bude_deck_info": (ci, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "bude_energies": (ci, [vp, vp, i64, vp, ctypes.POINTER(Options), vp]),
+        "bude_energies_batched": (ci, [ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                       ctypes.POINTER(i64), ctypes.POINTER(vp), i32,
+                                       ctypes.POINTER(Options), vp]),
+        "bude_pose_grad": (ci, [vp, vp, i64, vp, vp, ctypes.POINTER(Options), vp]),
+        "bude_get_default_options": (ci, [i32, ctypes.POINTER(Options)]),
+        "bude_set_default_options": (ci, [ctypes.POINTER(Options)]),
+        "bude_last_launch_count": (i64, []),
+        "bude_status_string": (ctypes.c_char_p, [ci]),
+        "bude_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions include/bude.h declares."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bude_[a-z_0-9]+)\s*\(", text)))
+
+
+def _check(rc: int):
+    if rc != OK:
+        lib = load()
+        raise BudeError(rc, f"{lib.bude_status_string(rc).decode()}: "
+                            f"{lib.bude_last_error().decode()}")
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def launch_count() -> int:
+    """Kernels the last compute call on this thread enqueued."""
+    return int(load().bude_last_launch_count())
+
+
+@dataclass
+class LaunchOptions:
+    variant: int = FP32_IEEE
+    ppwi: int = 0
+    block: int = 0
+    tile: int = 0
+    ctas_per_sm: int = 0
+
+    def c(self) -> Options:
+        v = VARIANTS[self.variant] if isinstance(self.variant, str) else self.variant
+        return Options(v, self.ppwi, self.block, self.tile, self.ctas_per_sm)
+
+
+def _opts(opts=None, **kw) -> Options:
+    if opts is None:
+        opts = LaunchOptions(**kw)
+    elif kw:
+        raise TypeError("pass either opts or keyword options")
+    return opts.c() if isinstance(opts, LaunchOptions) else opts
+
+
+def default_options(variant) -> LaunchOptions:
+    v = VARIANTS[variant] if isinstance(variant, str) else variant
+    o = Options()
+    _check(load().bude_get_default_options(v, ctypes.byref(o)))
+    return LaunchOptions(o.variant, o.ppwi, o.block, o.tile, o.ctas_per_sm)
+
+
+def set_default_options(opts: LaunchOptions):
+    o = opts.c()
+    _check(load().bude_set_default_options(ctypes.byref(o)))
+
+
+def pack_atoms(xyz, types) -> np.ndarray:
+    """[n][4] float32 records: x, y, z and the int32 type in the fourth word."""
+    xyz = np.ascontiguousarray(xyz, np.float32).reshape(-1, 3)
+    t = np.ascontiguousarray(types, np.int32).reshape(-1)
+    out = np.empty((xyz.shape[0], 4), np.float32)
+    out[:, :3] = xyz
+    out[:, 3] = t.view(np.float32)
+    return out
+
+
+def pack_forcefield(radius, hardness, elsc, hbtype) -> np.ndarray:
+    """[n_types][4] float32 rows: radius, hardness, elsc, hbtype (int32 bits)."""
+    n = len(radius)
+    out = np.empty((n, 4), np.float32)
+    out[:, 0] = radius
+    out[:, 1] = hardness
+    out[:, 2] = elsc
+    out[:, 3] = np.ascontiguousarray(hbtype, np.int32).view(np.float32)
+    return out
+
+
+class Deck:
+    """A deck on the current CUDA device (owns the library's deck handle)."""
+
+    def __init__(self, deck: dict, device=None, stream=None):
+        lib = load()
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        lig = torch.from_numpy(pack_atoms(deck["lig_xyz"], deck["lig_type"])).to(dev)
+        pro = torch.from_numpy(pack_atoms(deck["pro_xyz"], deck["pro_type"])).to(dev)
+        ff = torch.from_numpy(pack_forcefield(deck["radius"], deck["hardness"], deck["elsc"],
+                                              deck["hbtype"])).to(dev)
+        self.device = dev
+        self.n_lig, self.n_pro, self.n_types = lig.shape[0], pro.shape[0], ff.shape[0]
+        desc = DeckDesc(self.n_lig, self.n_pro, self.n_types,
+                        lig.data_ptr() if self.n_lig else None,
+                        pro.data_ptr() if self.n_pro else None, ff.data_ptr())
+        h = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            rc = lib.bude_create_deck(ctypes.byref(desc), _stream_ptr(stream), ctypes.byref(h))
+        _check(rc)
+        self._h = h
+        rows = ctypes.c_int32()
+        _check(lib.bude_deck_info(h, None, None, None, ctypes.byref(rows)))
+        self.n_rows = rows.value
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("deck was closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().bude_destroy_deck(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check_poses(poses: torch.Tensor, deck: Deck):
+    if not isinstance(poses, torch.Tensor) or poses.dtype != torch.float32:
+        raise TypeError("poses must be a float32 torch tensor")
+    if poses.dim() != 2 or poses.shape[0] != 6:
+        raise ValueError(f"poses must be [6, n], got {tuple(poses.shape)}")
+    if poses.device != deck.device:
+        raise ValueError(f"poses on {poses.device}, deck on {deck.device}")
+    if not poses.is_contiguous():
+        raise ValueError("poses must be contiguous")
+
+
+def energies(deck: Deck, poses: torch.Tensor, out: torch.Tensor | None = None,
+             opts=None, stream=None, **kw) -> torch.Tensor:
+    """Per-pose energies (float32 [n]) of device poses [6, n]."""
+    _check_poses(poses, deck)
+    n = poses.shape[1]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=poses.device)
+    elif out.shape != (n,) or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 [n] tensor")
+    o = _opts(opts, **kw)
+    rc = load().bude_energies(deck.handle, ctypes.c_void_p(poses.data_ptr()), n,
+                              ctypes.c_void_p(out.data_ptr()), ctypes.byref(o),
+                              _stream_ptr(stream))
+    _check(rc)
+    return out
+
+
+def energies_batched(decks, poses, outs=None, opts=None, stream=None, **kw):
+    """Energies of several decks in one persistent, graph-replayed launch."""
+    m = len(decks)
+    if len(poses) != m:
+        raise ValueError("one poses tensor per deck")
+    for d, p in zip(decks, poses):
+        _check_poses(p, d)
+    if outs is None:
+        outs = [torch.empty(p.shape[1], dtype=torch.float32, device=p.device) for p in poses]
+    VP = ctypes.c_void_p * m
+    hd = VP(*[d.handle.value for d in decks])
+    hp = VP(*[p.data_ptr() for p in poses])
+    ho = VP(*[o.data_ptr() for o in outs])
+    hn = (ctypes.c_int64 * m)(*[p.shape[1] for p in poses])
+    o = _opts(opts, **kw)
+    rc = load().bude_energies_batched(hd, hp, hn, ho, m, ctypes.byref(o), _stream_ptr(stream))
+    _check(rc)
+    return outs
+
+
+def pose_grad(deck: Deck, poses: torch.Tensor, want_energy: bool = True, opts=None,
+              stream=None, **kw):
+    """(energies [n] or None, d energy / d pose [6, n]) from the adjoint kernel."""
+    _check_poses(poses, deck)
+    n = poses.shape[1]
+    E = torch.empty(n, dtype=torch.float32, device=poses.device) if want_energy else None
+    G = torch.empty((6, n), dtype=torch.float32, device=poses.device)
+    o = _opts(opts, **kw)
+    rc = load().bude_pose_grad(deck.handle, ctypes.c_void_p(poses.data_ptr()), n,
+                               ctypes.c_void_p(E.data_ptr()) if E is not None else None,
+                               ctypes.c_void_p(G.data_ptr()), ctypes.byref(o),
+                               _stream_ptr(stream))
+    _check(rc)
+    return E, G
+
+
+class PoseEnergy(torch.autograd.Function):
+    """energies = PoseEnergy.apply(poses, deck, opts); backward uses the adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, poses, deck, opts=None):
+        p = poses.detach().contiguous()
+        E, G = pose_grad(deck, p, want_energy=True, opts=opts)
+        ctx.save_for_backward(G)
+        return E
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (G,) = ctx.saved_tensors
+        return G * grad_out.unsqueeze(0), None, None
+
+
+def refine(deck: Deck, poses: torch.Tensor, steps: int = 10, lr: float = 1e-3, opts=None):
+    """Plain gradient descent on the poses; returns (poses, energy history)."""
+    p = poses.detach().clone().requires_grad_(True)
+    hist = []
+    for _ in range(steps):
+        E = PoseEnergy.apply(p, deck, opts)
+        hist.append(E.detach().clone())
+        E.sum().backward()
+        with torch.no_grad():
+            p -= lr * p.grad
+            p.grad = None
+    with torch.no_grad():
+        hist.append(energies(deck, p.detach().contiguous(), opts=opts))
+    return p.detach(), hist

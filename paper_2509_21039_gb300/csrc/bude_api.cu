@@ -1,0 +1,670 @@
+// Host side of libbude.so: the C ABI declared in include/bude.h.
+//
+// Decks own repacked device copies of their inputs and a growable scratch
+// workspace (cross-CTA partial sums and arrival tickets of the persistent
+// kernel).  Launch planning -- the flat work space, the persistent grid and
+// the shared-memory carve-up -- happens here; all arithmetic of the path runs
+// in the kernels.
+#include <algorithm>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "bude_internal.h"
+
+using namespace bude;
+
+struct bude_deck {
+    int device = 0;
+    int n_lig = 0, n_pro = 0, n_types = 0, n_rows = 0;
+    float4* pro = nullptr;   // [n_pro]
+    float4* lig = nullptr;   // [n_lig] row-mapped
+    PairF* tabF = nullptr;   // [n_rows][n_types]
+    PairG* tabG = nullptr;
+    PairD* tabD = nullptr;
+    int* row_type = nullptr; // [n_rows]
+    // scratch workspace of the plain and adjoint calls
+    double* partial = nullptr;
+    size_t partial_bytes = 0;
+    unsigned* counter = nullptr;
+    size_t counter_count = 0;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+thread_local int64_t g_launches = 0;
+
+std::mutex g_opt_mutex;
+bude_options g_default[4] = {
+    {BUDE_FP32_IEEE, 8, 256, 0, 1},
+    {BUDE_FP32_FAST, 8, 256, 0, 1},
+    {BUDE_FP32_COMP, 8, 256, 0, 1},
+    {BUDE_FP64, 2, 256, 0, 1},
+};
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(BUDE_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(BUDE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+struct DeviceInfo {
+    int sms = 0;
+    size_t smem_optin = 0;   // max dynamic + static per block
+    size_t smem_per_sm = 0;
+    size_t reserved_per_block = 0;
+};
+
+DeviceInfo device_info(int dev)
+{
+    static std::mutex m;
+    static std::map<int, DeviceInfo> cache;
+    std::lock_guard<std::mutex> lk(m);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    DeviceInfo d;
+    cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    d.smem_optin = (size_t)v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    d.smem_per_sm = (size_t)v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    d.reserved_per_block = (size_t)v;
+    cache[dev] = d;
+    return d;
+}
+
+const void* kernel_for(int variant, int P, bool G)
+{
+    switch (variant) {
+    case BUDE_FP32_IEEE: return kernel_ieee(P, G);
+    case BUDE_FP32_FAST: return kernel_fast(P, G);
+    case BUDE_FP32_COMP: return kernel_comp(P, G);
+    case BUDE_FP64: return kernel_f64(P, G);
+    }
+    return nullptr;
+}
+
+// Bytes of one type-pair record for a variant / mode.
+size_t record_bytes(int variant, bool G)
+{
+    if (variant == BUDE_FP64) return sizeof(PairD);
+    return G ? sizeof(PairG) : sizeof(PairF);
+}
+
+// Dynamic shared memory of pose_kernel before the pair table and protein
+// chunk: max(transforms, warp partials) + final sums.  Mirrors the kernel.
+size_t smem_fixed(int variant, int P, bool G, int block)
+{
+    const size_t TP = 32u * (size_t)P;
+    const size_t W = (size_t)block / 32;
+    const size_t treal = variant == BUDE_FP64 ? 8 : 4;
+    const size_t tacc = (variant == BUDE_FP64 || variant == BUDE_FP32_COMP) ? 8 : 4;
+    size_t regA = std::max(12 * TP * treal, W * TP * tacc);
+    regA = (regA + 15) & ~size_t(15);
+    const size_t NV = G ? 7 : 1;
+    return regA + NV * TP * 8;
+}
+
+// Static shared memory of the kernel (Instance + flag), rounded up.
+constexpr size_t kStaticSmem = 256;
+
+struct Resolved {
+    int variant, P, block, tile, cps;
+};
+
+int resolve_options(const bude_options* o, bool G, Resolved* r)
+{
+    int variant = o ? o->variant : BUDE_FP32_IEEE;
+    if (variant < 0 || variant > 3) return fail(BUDE_ERR_INVALID_ARG, "unknown variant %d", variant);
+    bude_options d;
+    {
+        std::lock_guard<std::mutex> lk(g_opt_mutex);
+        d = g_default[variant];
+    }
+    r->variant = variant;
+    r->P = (o && o->ppwi) ? o->ppwi : d.ppwi;
+    r->block = (o && o->block) ? o->block : d.block;
+    r->tile = (o && o->tile) ? o->tile : d.tile;
+    r->cps = (o && o->ctas_per_sm) ? o->ctas_per_sm : d.ctas_per_sm;
+    if (G && variant != BUDE_FP64 && r->P > 8) r->P = 8;
+    if (G && variant == BUDE_FP64 && r->P > 4) r->P = 4;
+    if (r->block < 64 || r->block > 1024 || r->block % 32)
+        return fail(BUDE_ERR_INVALID_ARG, "block %d: need a multiple of 32 in [64, 1024]", r->block);
+    if (r->tile < 0) return fail(BUDE_ERR_INVALID_ARG, "tile %d < 0", r->tile);
+    if (r->cps < 1 || r->cps > 32) return fail(BUDE_ERR_INVALID_ARG, "ctas_per_sm %d", r->cps);
+    if (!kernel_for(variant, r->P, G))
+        return fail(BUDE_ERR_UNSUPPORTED, "poses per thread %d not built for variant %d%s", r->P,
+                    variant, G ? " (adjoint)" : "");
+    return BUDE_OK;
+}
+
+// Shared memory one CTA may use when cps CTAs share an SM.
+size_t smem_budget(const DeviceInfo& di, int cps)
+{
+    size_t per = di.smem_per_sm / (size_t)cps;
+    per = per > di.reserved_per_block ? per - di.reserved_per_block : 0;
+    return std::min(per, di.smem_optin) - kStaticSmem;
+}
+
+struct InstanceShape {
+    int n_lig, n_pro, n_types, n_rows;
+    long long n_poses;
+};
+
+// Protein chunk length for one instance, or -1 when even the table does not fit.
+int chunk_for(const InstanceShape& s, const Resolved& r, bool G, size_t budget)
+{
+    const size_t fixed = smem_fixed(r.variant, r.P, G, r.block);
+    const size_t table = (size_t)s.n_rows * s.n_types * record_bytes(r.variant, G);
+    if (fixed + table + 16 * 32 > budget) return -1;
+    size_t cap = (budget - fixed - table) / 16;
+    int want = s.n_pro;
+    if (r.tile > 0) want = std::min(want, r.tile);
+    int ch = (int)std::min<size_t>((size_t)std::max(want, 1), cap);
+    return std::max(ch, 1);
+}
+
+struct Plan {
+    std::vector<Instance> inst;
+    long long n_total = 0;
+    long long n_tiles = 0;
+    size_t smem = 0;
+    int grid = 0;
+    const void* fn = nullptr;
+};
+
+// Build the launch of a set of instances; instances without work are left
+// out (the caller zero-fills their outputs).
+int make_plan(const std::vector<const bude_deck*>& decks, const std::vector<const float*>& poses,
+              const std::vector<long long>& n, const std::vector<float*>& out,
+              const std::vector<float*>& grad, const Resolved& r, bool G, int dev, Plan* pl)
+{
+    const DeviceInfo di = device_info(dev);
+    const size_t budget = smem_budget(di, r.cps);
+    const long long TP = 32ll * r.P;
+    pl->inst.clear();
+    long long k = 0, tiles = 0;
+    size_t smem_max = 0;
+    for (size_t i = 0; i < decks.size(); ++i) {
+        const bude_deck* d = decks[i];
+        const long long K = (long long)d->n_lig * d->n_pro;
+        if (n[i] == 0 || K == 0) continue;
+        InstanceShape s{d->n_lig, d->n_pro, d->n_types, d->n_rows, n[i]};
+        const int ch = chunk_for(s, r, G, budget);
+        if (ch < 1)
+            return fail(BUDE_ERR_UNSUPPORTED,
+                        "type-pair table of %d x %d does not fit in shared memory", d->n_rows,
+                        d->n_types);
+        Instance I;
+        memset(&I, 0, sizeof I);
+        I.pro = d->pro;
+        I.lig = d->lig;
+        I.pair = r.variant == BUDE_FP64 ? (const void*)d->tabD
+                                        : (G ? (const void*)d->tabG : (const void*)d->tabF);
+        I.poses = poses[i];
+        I.out = out[i];
+        I.grad = G ? grad[i] : nullptr;
+        I.n_poses = n[i];
+        const long long nt = (n[i] + TP - 1) / TP;
+        I.k_begin = k;
+        I.k_end = k + nt * K;
+        I.tile_begin = tiles;
+        I.n_lig = d->n_lig;
+        I.n_pro = d->n_pro;
+        I.n_types = d->n_types;
+        I.n_rows = d->n_rows;
+        I.chunk = ch;
+        k = I.k_end;
+        tiles += nt;
+        const size_t sm = smem_fixed(r.variant, r.P, G, r.block) +
+                          (size_t)d->n_rows * d->n_types * record_bytes(r.variant, G) +
+                          16 * (size_t)ch;
+        smem_max = std::max(smem_max, sm);
+        pl->inst.push_back(I);
+    }
+    pl->n_total = k;
+    pl->n_tiles = tiles;
+    pl->smem = smem_max;
+    pl->fn = kernel_for(r.variant, r.P, G);
+    if (pl->inst.empty()) return BUDE_OK;
+    CK(cudaFuncSetAttribute(pl->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem),
+       "cudaFuncSetAttribute");
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pl->fn, r.block, pl->smem),
+       "occupancy query");
+    if (occ < 1)
+        return fail(BUDE_ERR_UNSUPPORTED, "block %d with %zu B shared memory cannot be resident",
+                    r.block, pl->smem);
+    occ = std::min(occ, r.cps);
+    long long grid = (long long)di.sms * occ;
+    if (grid > pl->n_total) grid = pl->n_total;
+    pl->grid = (int)std::max(1ll, grid);
+    return BUDE_OK;
+}
+
+size_t partial_bytes_for(const Plan& pl, const Resolved& r, bool G)
+{
+    const size_t NV = G ? 7 : 1;
+    return ((size_t)pl.grid + (size_t)pl.n_tiles) * NV * 32u * (size_t)r.P * sizeof(double);
+}
+
+int ensure_workspace(double** partial, size_t* pbytes, unsigned** counter, size_t* ccount,
+                     size_t need_bytes, size_t need_count, cudaStream_t s)
+{
+    if (need_bytes > *pbytes) {
+        if (*partial) {
+            CK(cudaStreamSynchronize(s), "workspace sync");
+            cudaFree(*partial);
+            *partial = nullptr;
+            *pbytes = 0;
+        }
+        size_t b = std::max(need_bytes, (size_t)1 << 16);
+        CK(cudaMalloc((void**)partial, b), "workspace allocation");
+        *pbytes = b;
+    }
+    if (need_count > *ccount) {
+        if (*counter) {
+            CK(cudaStreamSynchronize(s), "workspace sync");
+            cudaFree(*counter);
+            *counter = nullptr;
+            *ccount = 0;
+        }
+        size_t c = std::max(need_count, (size_t)1024);
+        CK(cudaMalloc((void**)counter, c * sizeof(unsigned)), "workspace allocation");
+        CK(cudaMemsetAsync(*counter, 0, c * sizeof(unsigned), s), "workspace clear");
+        *ccount = c;
+    }
+    return BUDE_OK;
+}
+
+int launch_plan(const Plan& pl, const Resolved& r, const Instance* dev_table, double* partial,
+                unsigned* counter, cudaStream_t s)
+{
+    Args a;
+    memset(&a, 0, sizeof a);
+    a.n_inst = (int)pl.inst.size();
+    if (a.n_inst == 1) a.single = pl.inst[0];
+    a.table = dev_table;
+    a.n_total = pl.n_total;
+    a.partial = partial;
+    a.counter = counter;
+    void* params[] = {&a};
+    CK(cudaLaunchKernel(pl.fn, dim3(pl.grid), dim3(r.block), params, pl.smem, s), "kernel launch");
+    ++g_launches;
+    return BUDE_OK;
+}
+
+int current_device(int* dev)
+{
+    CK(cudaGetDevice(dev), "cudaGetDevice");
+    return BUDE_OK;
+}
+
+// Single-deck energies or adjoint.
+int run_single(bude_deck* deck, const float* poses, int64_t n, float* energies, float* grad,
+               const bude_options* opts, void* stream, bool G)
+{
+    g_launches = 0;
+    if (!deck) return fail(BUDE_ERR_INVALID_ARG, "deck is NULL");
+    if (n < 0) return fail(BUDE_ERR_INVALID_ARG, "n = %lld < 0", (long long)n);
+    if (n == 0) return BUDE_OK;
+    if (!poses) return fail(BUDE_ERR_INVALID_ARG, "poses is NULL");
+    if (!G && !energies) return fail(BUDE_ERR_INVALID_ARG, "energies is NULL");
+    if (G && !grad) return fail(BUDE_ERR_INVALID_ARG, "grad is NULL");
+    Resolved r;
+    int rc = resolve_options(opts, G, &r);
+    if (rc) return rc;
+    int dev;
+    if ((rc = current_device(&dev))) return rc;
+    if (dev != deck->device)
+        return fail(BUDE_ERR_INVALID_ARG, "deck lives on device %d, current device is %d",
+                    deck->device, dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long K = (long long)deck->n_lig * deck->n_pro;
+    if (K == 0) {
+        if (energies) CK(cudaMemsetAsync(energies, 0, (size_t)n * sizeof(float), s), "memset");
+        if (G) CK(cudaMemsetAsync(grad, 0, (size_t)n * 6 * sizeof(float), s), "memset");
+        return BUDE_OK;
+    }
+    Plan pl;
+    rc = make_plan({deck}, {poses}, {(long long)n}, {energies}, {grad}, r, G, dev, &pl);
+    if (rc) return rc;
+    rc = ensure_workspace(&deck->partial, &deck->partial_bytes, &deck->counter,
+                          &deck->counter_count, partial_bytes_for(pl, r, G), (size_t)pl.n_tiles,
+                          s);
+    if (rc) return rc;
+    return launch_plan(pl, r, nullptr, deck->partial, deck->counter, s);
+}
+
+// ---- batched plans -------------------------------------------------------
+
+struct BatchKey {
+    int dev;
+    Resolved r;
+    std::vector<const void*> ptrs;  // deck, poses, out per instance
+    std::vector<long long> n;
+    bool operator<(const BatchKey& o) const
+    {
+        if (dev != o.dev) return dev < o.dev;
+        if (memcmp(&r, &o.r, sizeof r)) return memcmp(&r, &o.r, sizeof r) < 0;
+        if (ptrs != o.ptrs) return ptrs < o.ptrs;
+        return n < o.n;
+    }
+};
+
+struct BatchPlan {
+    Plan pl;
+    Resolved r;
+    std::vector<const bude_deck*> decks;
+    Instance* dev_table = nullptr;
+    double* partial = nullptr;
+    size_t partial_bytes = 0;
+    unsigned* counter = nullptr;
+    size_t counter_count = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+    ~BatchPlan()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (dev_table) cudaFree(dev_table);
+        if (partial) cudaFree(partial);
+        if (counter) cudaFree(counter);
+    }
+};
+
+std::mutex g_batch_mutex;
+std::map<BatchKey, BatchPlan*> g_batches;
+
+void drop_batches_using(const bude_deck* d)
+{
+    std::lock_guard<std::mutex> lk(g_batch_mutex);
+    for (auto it = g_batches.begin(); it != g_batches.end();) {
+        const auto& ds = it->second->decks;
+        if (std::find(ds.begin(), ds.end(), d) != ds.end()) {
+            delete it->second;
+            it = g_batches.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* bude_status_string(int status)
+{
+    switch (status) {
+    case BUDE_OK: return "ok";
+    case BUDE_ERR_INVALID_ARG: return "invalid argument";
+    case BUDE_ERR_CUDA: return "CUDA error";
+    case BUDE_ERR_OOM: return "out of device memory";
+    case BUDE_ERR_UNSUPPORTED: return "unsupported shape or option";
+    case BUDE_ERR_DEVICE_FLAG: return "device-side check failed";
+    }
+    return "unknown status";
+}
+
+const char* bude_last_error(void) { return g_last_error.c_str(); }
+
+int64_t bude_last_launch_count(void) { return g_launches; }
+
+int bude_get_default_options(int32_t variant, bude_options* out)
+{
+    if (!out || variant < 0 || variant > 3) return fail(BUDE_ERR_INVALID_ARG, "bad arguments");
+    std::lock_guard<std::mutex> lk(g_opt_mutex);
+    *out = g_default[variant];
+    return BUDE_OK;
+}
+
+int bude_set_default_options(const bude_options* o)
+{
+    if (!o || o->variant < 0 || o->variant > 3) return fail(BUDE_ERR_INVALID_ARG, "bad options");
+    Resolved r;
+    int rc = resolve_options(o, false, &r);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_opt_mutex);
+    g_default[o->variant] = {r.variant, r.P, r.block, r.tile, r.cps};
+    return BUDE_OK;
+}
+
+int bude_create_deck(const bude_deck_desc* desc, void* stream, bude_deck** out)
+{
+    g_launches = 0;
+    if (!out) return fail(BUDE_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!desc) return fail(BUDE_ERR_INVALID_ARG, "desc is NULL");
+    if (desc->n_lig < 0 || desc->n_pro < 0)
+        return fail(BUDE_ERR_INVALID_ARG, "negative atom count");
+    if (desc->n_types < 1 || desc->n_types > BUDE_MAX_TYPES)
+        return fail(BUDE_ERR_INVALID_ARG, "n_types %d outside 1..%d", desc->n_types,
+                    BUDE_MAX_TYPES);
+    if ((desc->n_lig && !desc->lig_xyzt) || (desc->n_pro && !desc->pro_xyzt) || !desc->ff)
+        return fail(BUDE_ERR_INVALID_ARG, "NULL array with non-zero size");
+    cudaStream_t s = (cudaStream_t)stream;
+    bude_deck* d = new bude_deck;
+    int rc = current_device(&d->device);
+    if (rc) { delete d; return rc; }
+    d->n_lig = desc->n_lig;
+    d->n_pro = desc->n_pro;
+    d->n_types = desc->n_types;
+    struct Tmp { unsigned err; int n_rows; };
+    Tmp* tmp = nullptr;
+    auto cleanup = [&](int code) {
+        if (tmp) cudaFree(tmp);
+        bude_destroy_deck(d);
+        return code;
+    };
+#define CKD(call, what)                                               \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return cleanup(cuda_fail(e_, what));   \
+    } while (0)
+    const size_t nl = std::max(1, d->n_lig), np = std::max(1, d->n_pro);
+    const size_t pairs = (size_t)std::max(1, d->n_lig < d->n_types ? d->n_lig : d->n_types) *
+                         d->n_types;
+    CKD(cudaMalloc((void**)&d->pro, np * sizeof(float4)), "deck allocation");
+    CKD(cudaMalloc((void**)&d->lig, nl * sizeof(float4)), "deck allocation");
+    CKD(cudaMalloc((void**)&d->tabF, pairs * sizeof(PairF)), "deck allocation");
+    CKD(cudaMalloc((void**)&d->tabG, pairs * sizeof(PairG)), "deck allocation");
+    CKD(cudaMalloc((void**)&d->tabD, pairs * sizeof(PairD)), "deck allocation");
+    CKD(cudaMalloc((void**)&d->row_type, (size_t)d->n_types * sizeof(int)), "deck allocation");
+    CKD(cudaMalloc((void**)&tmp, sizeof(Tmp)), "deck allocation");
+    CKD(cudaMemsetAsync(tmp, 0, sizeof(Tmp), s), "memset");
+    CKD(launch_pack_protein((const float4*)desc->pro_xyzt, d->pro, d->n_pro, d->n_types,
+                            &tmp->err, s),
+        "protein packing launch");
+    CKD(launch_build_tables((const float4*)desc->lig_xyzt, d->n_lig, (const float4*)desc->ff,
+                            d->n_types, d->lig, d->tabF, d->tabG, d->tabD, d->row_type,
+                            &tmp->n_rows, &tmp->err, s),
+        "pair table launch");
+    g_launches += (d->n_pro > 0) ? 2 : 1;
+    Tmp h{0, 0};
+    CKD(cudaMemcpyAsync(&h, tmp, sizeof h, cudaMemcpyDeviceToHost, s), "readback");
+    CKD(cudaStreamSynchronize(s), "deck synchronisation");
+#undef CKD
+    cudaFree(tmp);
+    tmp = nullptr;
+    if (h.err) {
+        std::string why;
+        if (h.err & 1u) why += " atom type outside [0, n_types);";
+        if (h.err & 2u) why += " non-finite atom coordinate;";
+        if (h.err & 4u) why += " forcefield row with radius <= 0, a non-finite value or hbtype not in {0,1,2};";
+        bude_destroy_deck(d);
+        return fail(BUDE_ERR_INVALID_ARG, "deck rejected:%s", why.c_str());
+    }
+    d->n_rows = h.n_rows;
+    *out = d;
+    return BUDE_OK;
+}
+
+int bude_destroy_deck(bude_deck* d)
+{
+    if (!d) return BUDE_OK;
+    drop_batches_using(d);
+    cudaDeviceSynchronize();
+    cudaFree(d->pro);
+    cudaFree(d->lig);
+    cudaFree(d->tabF);
+    cudaFree(d->tabG);
+    cudaFree(d->tabD);
+    cudaFree(d->row_type);
+    cudaFree(d->partial);
+    cudaFree(d->counter);
+    delete d;
+    return BUDE_OK;
+}
+
+int bude_deck_info(const bude_deck* d, int32_t* n_lig, int32_t* n_pro, int32_t* n_types,
+                   int32_t* n_rows)
+{
+    if (!d) return fail(BUDE_ERR_INVALID_ARG, "deck is NULL");
+    if (n_lig) *n_lig = d->n_lig;
+    if (n_pro) *n_pro = d->n_pro;
+    if (n_types) *n_types = d->n_types;
+    if (n_rows) *n_rows = d->n_rows;
+    return BUDE_OK;
+}
+
+int bude_energies(bude_deck* deck, const float* poses, int64_t n, float* energies,
+                  const bude_options* opts, void* stream)
+{
+    return run_single(deck, poses, n, energies, nullptr, opts, stream, false);
+}
+
+int bude_pose_grad(bude_deck* deck, const float* poses, int64_t n, float* energies, float* grad,
+                   const bude_options* opts, void* stream)
+{
+    return run_single(deck, poses, n, energies, grad, opts, stream, true);
+}
+
+int bude_energies_batched(bude_deck* const* decks, const float* const* poses, const int64_t* n,
+                          float* const* energies, int32_t count, const bude_options* opts,
+                          void* stream)
+{
+    g_launches = 0;
+    if (count < 0) return fail(BUDE_ERR_INVALID_ARG, "count %d < 0", count);
+    if (count == 0) return BUDE_OK;
+    if (!decks || !poses || !n || !energies)
+        return fail(BUDE_ERR_INVALID_ARG, "NULL argument array");
+    Resolved r;
+    int rc = resolve_options(opts, false, &r);
+    if (rc) return rc;
+    int dev;
+    if ((rc = current_device(&dev))) return rc;
+    BatchKey key;
+    key.dev = dev;
+    key.r = r;
+    for (int i = 0; i < count; ++i) {
+        if (!decks[i]) return fail(BUDE_ERR_INVALID_ARG, "decks[%d] is NULL", i);
+        if (n[i] < 0) return fail(BUDE_ERR_INVALID_ARG, "n[%d] < 0", i);
+        if (n[i] > 0 && (!poses[i] || !energies[i]))
+            return fail(BUDE_ERR_INVALID_ARG, "NULL poses or energies for instance %d", i);
+        if (decks[i]->device != dev)
+            return fail(BUDE_ERR_INVALID_ARG, "decks[%d] lives on another device", i);
+        key.ptrs.push_back(decks[i]);
+        key.ptrs.push_back(poses[i]);
+        key.ptrs.push_back(energies[i]);
+        key.n.push_back(n[i]);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    BatchPlan* bp = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_batch_mutex);
+        auto it = g_batches.find(key);
+        if (it != g_batches.end()) bp = it->second;
+    }
+    if (!bp) {
+        bp = new BatchPlan;
+        bp->r = r;
+        std::vector<const bude_deck*> dv(decks, decks + count);
+        std::vector<const float*> pv(poses, poses + count);
+        std::vector<long long> nv(n, n + count);
+        std::vector<float*> ov(energies, energies + count);
+        std::vector<float*> gv(count, nullptr);
+        bp->decks = dv;
+        rc = make_plan(dv, pv, nv, ov, gv, r, false, dev, &bp->pl);
+        if (rc) { delete bp; return rc; }
+        const Plan& pl = bp->pl;
+        auto bail = [&](int code) { delete bp; return code; };
+        if (!pl.inst.empty()) {
+            cudaError_t e = cudaMalloc((void**)&bp->dev_table, pl.inst.size() * sizeof(Instance));
+            if (e) return bail(cuda_fail(e, "plan allocation"));
+            e = cudaMemcpy(bp->dev_table, pl.inst.data(), pl.inst.size() * sizeof(Instance),
+                           cudaMemcpyHostToDevice);
+            if (e) return bail(cuda_fail(e, "plan upload"));
+            rc = ensure_workspace(&bp->partial, &bp->partial_bytes, &bp->counter,
+                                  &bp->counter_count, partial_bytes_for(pl, r, false),
+                                  (size_t)pl.n_tiles, s);
+            if (rc) return bail(rc);
+            e = cudaStreamSynchronize(s);
+            if (e) return bail(cuda_fail(e, "plan synchronisation"));
+        }
+        // capture: zero-fill of instances without work, then the persistent launch
+        cudaStream_t cs;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e) return bail(cuda_fail(e, "capture stream"));
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e) { cudaStreamDestroy(cs); return bail(cuda_fail(e, "begin capture")); }
+        int launches = 0;
+        for (int i = 0; i < count; ++i) {
+            const long long K = (long long)decks[i]->n_lig * decks[i]->n_pro;
+            if (n[i] > 0 && K == 0) {
+                cudaMemsetAsync(energies[i], 0, (size_t)n[i] * sizeof(float), cs);
+            }
+        }
+        int lrc = BUDE_OK;
+        if (!pl.inst.empty()) {
+            int64_t saved = g_launches;
+            lrc = launch_plan(pl, r, bp->dev_table, bp->partial, bp->counter, cs);
+            launches = (int)(g_launches - saved);
+        }
+        e = cudaStreamEndCapture(cs, &bp->graph);
+        cudaStreamDestroy(cs);
+        if (lrc) return bail(lrc);
+        if (e) return bail(cuda_fail(e, "end capture"));
+        e = cudaGraphInstantiate(&bp->exec, bp->graph, 0);
+        if (e) return bail(cuda_fail(e, "graph instantiation"));
+        bp->launches = launches;
+        std::lock_guard<std::mutex> lk(g_batch_mutex);
+        g_batches[key] = bp;
+    }
+    CK(cudaGraphLaunch(bp->exec, s), "graph launch");
+    g_launches = bp->launches;
+    return BUDE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Deck preparation kernels: validation, ligand-type compaction and the
+// type-pair parameter tables (the per-pair lookup of Eq. 3, built once per
+// deck instead of once per pair).
+#include "bude_internal.h"
+
+namespace bude {
+
+enum : unsigned {
+    kErrType = 1u,      // an atom type outside [0, n_types)
+    kErrCoord = 2u,     // a non-finite atom coordinate
+    kErrForceField = 4u // radius <= 0, a non-finite parameter or a bad hbtype
+};
+
+__global__ void pack_protein_kernel(const float4* __restrict__ src, float4* __restrict__ dst,
+                                    int n, int n_types, unsigned* err)
+{
+    unsigned bad = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float4 a = src[i];
+        int t = __float_as_int(a.w);
+        if (t < 0 || t >= n_types) bad |= kErrType;
+        if (!isfinite(a.x) || !isfinite(a.y) || !isfinite(a.z)) bad |= kErrCoord;
+        dst[i] = a;
+    }
+    if (bad) atomicOr(err, bad);
+}
+
+// Single CTA: forcefield checks, ligand row map and the three pair tables.
+__global__ void build_tables_kernel(const float4* __restrict__ lig_src, int n_lig,
+                                    const float4* __restrict__ ff, int n_types,
+                                    float4* __restrict__ lig_dst, PairF* __restrict__ tabF,
+                                    PairG* __restrict__ tabG, PairD* __restrict__ tabD,
+                                    int* __restrict__ row_type, int* n_rows_out, unsigned* err)
+{
+    __shared__ int s_row[BUDE_MAX_TYPES];   // type -> row, -1 unused
+    __shared__ int s_type[BUDE_MAX_TYPES];  // row -> type
+    __shared__ int s_nrows;
+    __shared__ unsigned s_err;
+    if (threadIdx.x == 0) { s_err = 0; s_nrows = 0; }
+    for (int t = threadIdx.x; t < n_types; t += blockDim.x) s_row[t] = -1;
+    __syncthreads();
+
+    unsigned bad = 0;
+    for (int t = threadIdx.x; t < n_types; t += blockDim.x) {
+        float4 f = ff[t];
+        int hb = __float_as_int(f.w);
+        if (!(f.x > 0.f) || !isfinite(f.x) || !isfinite(f.y) || !isfinite(f.z) || hb < 0 || hb > 2)
+            bad |= kErrForceField;
+    }
+    for (int l = threadIdx.x; l < n_lig; l += blockDim.x) {
+        float4 a = lig_src[l];
+        int t = __float_as_int(a.w);
+        if (t < 0 || t >= n_types) {
+            bad |= kErrType;
+        } else {
+            s_row[t] = 1;  // benign race: every writer stores the same value
+        }
+        if (!isfinite(a.x) || !isfinite(a.y) || !isfinite(a.z)) bad |= kErrCoord;
+    }
+    if (bad) atomicOr(&s_err, bad);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int r = 0;
+        for (int t = 0; t < n_types; ++t) {
+            if (s_row[t] == 1) { s_type[r] = t; s_row[t] = r; ++r; }
+            else s_row[t] = -1;
+        }
+        s_nrows = r;
+        *n_rows_out = r;
+        if (s_err) atomicOr(err, s_err);
+    }
+    __syncthreads();
+    if (s_err) return;
+    for (int l = threadIdx.x; l < n_lig; l += blockDim.x) {
+        float4 a = lig_src[l];
+        a.w = __int_as_float(s_row[__float_as_int(a.w)]);
+        lig_dst[l] = a;
+    }
+    const int rows = s_nrows;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) row_type[r] = s_type[r];
+    for (int i = threadIdx.x; i < rows * n_types; i += blockDim.x) {
+        const int ta = s_type[i / n_types], tb = i % n_types;
+        const float4 fa = ff[ta], fb = ff[tb];
+        const int ha = __float_as_int(fa.w), hb = __float_as_int(fb.w);
+        // combination rules, evaluated in FP64 and rounded once
+        const double R = (double)fa.x + (double)fb.x;
+        const double H = 0.5 * ((double)fa.y + (double)fb.y);
+        const double w = ((ha == 1 && hb == 2) || (ha == 2 && hb == 1)) ? 2.0 : 1.0;
+        const double cE = kKE * (double)fa.z * (double)fb.z * w;
+        const double S = ((ha != 0) != (hb != 0)) ? kKD : 0.0;
+        PairD d;
+        d.inv_r = 1.0 / R;
+        d.h = H;
+        d.ce = R / kDE + 1.0;
+        d.ke1 = -2.0 * cE;
+        d.ke0 = 3.0 * cE;
+        d.cd = R / kDD + 1.0;
+        d.kd1 = -2.0 * S;
+        d.kd0 = 3.0 * S;
+        tabD[i] = d;
+        PairF f;
+        f.inv_r = (float)d.inv_r; f.h = (float)d.h; f.ce = (float)d.ce; f.ke1 = (float)d.ke1;
+        f.ke0 = (float)d.ke0; f.cd = (float)d.cd; f.kd1 = (float)d.kd1; f.kd0 = (float)d.kd0;
+        tabF[i] = f;
+        PairG g;
+        g.inv_r = f.inv_r; g.h = f.h; g.ce = f.ce; g.ke1 = f.ke1;
+        g.ke0 = f.ke0; g.cd = f.cd; g.kd1 = f.kd1; g.kd0 = f.kd0;
+        g.hs = (float)(-2.0 * H * d.inv_r);
+        g.ae1 = (float)(-3.0 / kDE * d.ke1);
+        g.ae0 = (float)(-2.0 / kDE * d.ke0);
+        g.ad1 = (float)(-3.0 / kDD * d.kd1);
+        g.ad0 = (float)(-2.0 / kDD * d.kd0);
+        g.pad0 = g.pad1 = g.pad2 = 0.f;
+        tabG[i] = g;
+    }
+}
+
+cudaError_t launch_pack_protein(const float4* src, float4* dst, int n, int n_types,
+                                unsigned* err, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    int blocks = (n + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    pack_protein_kernel<<<blocks, 256, 0, s>>>(src, dst, n, n_types, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_tables(const float4* lig_src, int n_lig, const float4* ff, int n_types,
+                                float4* lig_dst, PairF* tabF, PairG* tabG, PairD* tabD,
+                                int* row_type, int* n_rows, unsigned* err, cudaStream_t s)
+{
+    build_tables_kernel<<<1, 512, 0, s>>>(lig_src, n_lig, ff, n_types, lig_dst, tabF, tabG,
+                                          tabD, row_type, n_rows, err);
+    return cudaGetLastError();
+}
+
+}  // namespace bude

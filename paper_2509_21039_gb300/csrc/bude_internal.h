@@ -1,0 +1,27 @@
+// Internal declarations shared by the host API and the kernel translation
+// units of libbude.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/bude.h"
+#include "bude_kernels.cuh"
+
+namespace bude {
+
+// Kernel entry of pose_kernel<V, P, G>, or nullptr when that combination is
+// not built.  Defined in the per-variant translation units.
+const void* kernel_ieee(int P, bool G);
+const void* kernel_fast(int P, bool G);
+const void* kernel_comp(int P, bool G);
+const void* kernel_f64(int P, bool G);
+
+cudaError_t launch_pack_protein(const float4* src, float4* dst, int n, int n_types,
+                                unsigned* err, cudaStream_t s);
+cudaError_t launch_build_tables(const float4* lig_src, int n_lig, const float4* ff, int n_types,
+                                float4* lig_dst, PairF* tabF, PairG* tabG, PairD* tabD,
+                                int* row_type, int* n_rows, unsigned* err, cudaStream_t s);
+
+}  // namespace bude

@@ -1,0 +1,37 @@
+// Instantiations of the persistent pose kernel, FP32 variant kIEEE.
+#include "bude_internal.h"
+
+namespace bude {
+
+template __global__ void pose_kernel<kIEEE, 1, false>(const Args);
+template __global__ void pose_kernel<kIEEE, 2, false>(const Args);
+template __global__ void pose_kernel<kIEEE, 4, false>(const Args);
+template __global__ void pose_kernel<kIEEE, 8, false>(const Args);
+template __global__ void pose_kernel<kIEEE, 16, false>(const Args);
+template __global__ void pose_kernel<kIEEE, 1, true>(const Args);
+template __global__ void pose_kernel<kIEEE, 2, true>(const Args);
+template __global__ void pose_kernel<kIEEE, 4, true>(const Args);
+template __global__ void pose_kernel<kIEEE, 8, true>(const Args);
+
+const void* kernel_ieee(int P, bool G)
+{
+    if (!G) {
+        switch (P) {
+        case 1: return (const void*)pose_kernel<kIEEE, 1, false>;
+        case 2: return (const void*)pose_kernel<kIEEE, 2, false>;
+        case 4: return (const void*)pose_kernel<kIEEE, 4, false>;
+        case 8: return (const void*)pose_kernel<kIEEE, 8, false>;
+        case 16: return (const void*)pose_kernel<kIEEE, 16, false>;
+        }
+    } else {
+        switch (P) {
+        case 1: return (const void*)pose_kernel<kIEEE, 1, true>;
+        case 2: return (const void*)pose_kernel<kIEEE, 2, true>;
+        case 4: return (const void*)pose_kernel<kIEEE, 4, true>;
+        case 8: return (const void*)pose_kernel<kIEEE, 8, true>;
+        }
+    }
+    return nullptr;
+}
+
+}  // namespace bude

@@ -1,0 +1,72 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every
+function include/bude.h declares; argument validation that happens before
+any CUDA call."""
+import ctypes
+
+import pytest
+
+from paper_2509_21039_gb300 import bude
+from paper_2509_21039_gb300 import build as build_mod
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_mod.build()
+    return bude.load()
+
+
+def test_header_declares_the_boundary():
+    names = bude.header_functions()
+    for n in ("bude_create_deck", "bude_destroy_deck", "bude_energies",
+              "bude_energies_batched", "bude_pose_grad", "bude_status_string"):
+        assert n in names
+
+
+def test_every_declared_function_is_exported(lib):
+    missing = [n for n in bude.header_functions() if not hasattr(lib, n)]
+    assert missing == []
+
+
+def test_status_strings(lib):
+    for code in (bude.OK, bude.ERR_INVALID_ARG, bude.ERR_CUDA, bude.ERR_OOM,
+                 bude.ERR_UNSUPPORTED, bude.ERR_DEVICE_FLAG):
+        s = lib.bude_status_string(code).decode()
+        assert s and s != "unknown status"
+    assert lib.bude_status_string(12345).decode() == "unknown status"
+
+
+def test_null_arguments_are_rejected_without_a_gpu(lib):
+    h = ctypes.c_void_p()
+    assert lib.bude_create_deck(None, None, ctypes.byref(h)) == bude.ERR_INVALID_ARG
+    assert h.value is None
+    desc = bude.DeckDesc(4, 4, 0, None, None, None)
+    assert lib.bude_create_deck(ctypes.byref(desc), None, ctypes.byref(h)) == bude.ERR_INVALID_ARG
+    desc = bude.DeckDesc(-1, 4, 3, None, None, None)
+    assert lib.bude_create_deck(ctypes.byref(desc), None, ctypes.byref(h)) == bude.ERR_INVALID_ARG
+    desc = bude.DeckDesc(4, 4, bude.MAX_TYPES + 1, None, None, None)
+    assert lib.bude_create_deck(ctypes.byref(desc), None, ctypes.byref(h)) == bude.ERR_INVALID_ARG
+    o = bude.Options()
+    assert lib.bude_energies(None, None, 10, None, ctypes.byref(o), None) == bude.ERR_INVALID_ARG
+    assert lib.bude_pose_grad(None, None, 10, None, None, ctypes.byref(o), None) == bude.ERR_INVALID_ARG
+    assert lib.bude_energies_batched(None, None, None, None, -1, None, None) == bude.ERR_INVALID_ARG
+    assert lib.bude_energies_batched(None, None, None, None, 0, None, None) == bude.OK
+    assert "NULL" in lib.bude_last_error().decode() or lib.bude_last_error()
+
+
+def test_default_options_roundtrip(lib):
+    for v in range(4):
+        o = bude.default_options(v)
+        assert o.variant == v and o.ppwi > 0 and o.block % 32 == 0
+    with pytest.raises(bude.BudeError):
+        bude.set_default_options(bude.LaunchOptions(variant=0, ppwi=3, block=256))
+    with pytest.raises(bude.BudeError):
+        bude.set_default_options(bude.LaunchOptions(variant=0, ppwi=8, block=100))
+    with pytest.raises(bude.BudeError):
+        bude.set_default_options(bude.LaunchOptions(variant=3, ppwi=16, block=256))
+
+
+def test_pack_atoms_keeps_type_bits():
+    import numpy as np
+    rec = bude.pack_atoms(np.array([[1.0, 2.0, 3.0]]), np.array([33]))
+    assert rec.dtype == np.float32 and rec.shape == (1, 4)
+    assert rec[0, 3:].view(np.int32)[0] == 33

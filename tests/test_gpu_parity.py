@@ -1,0 +1,367 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Error measure per pose: |E_gpu - E_ref| / max(A_ref, 1), A_ref = 0.5 sum |e|
+(the oracle's absolute-term sum).  Gates, from the arithmetic: FP32 with
+correctly rounded sqrt keeps every pair term within a few ulp (2^-23 ~ 1.2e-7
+relative) and sums of up to ~1e5 terms stay far inside 1e-5; the approximate
+sqrt/sin/cos of the fast variant adds ~2^-21 relative per term, gated at 1e-4.
+The FP64 variant computes in double and rounds once to the float32 output,
+so it must agree with the oracle to half an FP32 ulp of the result plus
+1e-12 of the scale (summation order).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_21039_gb300 import bude, synth
+
+pytestmark = pytest.mark.gpu
+
+GATE = {"ieee": 1e-5, "fast": 1e-4, "comp": 1e-5, "fp64": 1e-12}
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2509_21039_gb300 import build
+    build.build()
+    bude.load()
+
+
+def scaled_error(E, ref, A, variant=None):
+    d = np.abs(np.asarray(E, np.float64) - ref)
+    if variant == "fp64":
+        # remove the one rounding to the float32 output (half an ulp)
+        d = np.maximum(d - np.abs(ref) * 2.0 ** -24 * (1 + 1e-9), 0.0)
+    return d / np.maximum(A, 1.0)
+
+
+def run(deck_np, poses=None, variant="ieee", **kw):
+    deck = bude.Deck(deck_np, device=DEV)
+    P = torch.from_numpy(np.ascontiguousarray(poses if poses is not None else deck_np["poses"])).to(DEV)
+    E = bude.energies(deck, P, variant=variant, **kw)
+    torch.cuda.synchronize()
+    return E.cpu().numpy()
+
+
+def check(deck_np, variant="ieee", poses=None, **kw):
+    poses = poses if poses is not None else deck_np["poses"]
+    ref, A = oracle.energies(deck_np, poses, n_threads=-1, with_abs=True)
+    E = run(deck_np, poses, variant, **kw)
+    err = scaled_error(E, ref, A, variant)
+    assert err.max() <= GATE[variant], (variant, kw, err.max())
+    return E, ref, A
+
+
+# --- small decks: several tiles, ragged tails, every launch shape -----------
+
+@pytest.mark.parametrize("variant", ["ieee", "fast", "comp", "fp64"])
+def test_small_deck_all_variants(variant):
+    D = synth.make_deck(101, 16, 300, 34, 1000)
+    check(D, variant)
+
+
+@pytest.mark.parametrize("ppwi", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("block", [64, 256, 1024])
+def test_launch_shapes_ieee(ppwi, block):
+    D = synth.make_deck(102, 11, 257, 34, 777)
+    try:
+        check(D, "ieee", ppwi=ppwi, block=block)
+    except bude.BudeError as e:
+        # a block too large for this register count cannot be resident
+        assert e.code == bude.ERR_UNSUPPORTED and block == 1024
+
+
+@pytest.mark.parametrize("variant,ppwi", [("fast", 4), ("fast", 16), ("comp", 2), ("comp", 8),
+                                          ("fp64", 1), ("fp64", 4)])
+def test_launch_shapes_other_variants(variant, ppwi):
+    D = synth.make_deck(103, 9, 190, 34, 600)
+    check(D, variant, ppwi=ppwi, block=128)
+
+
+@pytest.mark.parametrize("tile", [32, 100, 257])
+@pytest.mark.parametrize("cps", [1, 2, 3])
+def test_protein_chunking_and_grid(tile, cps):
+    D = synth.make_deck(104, 13, 640, 34, 900)
+    check(D, "ieee", ppwi=4, block=128, tile=tile, ctas_per_sm=cps)
+
+
+def test_small_config_seed0_every_variant():
+    D = synth.make_deck(0, **synth.SMALL)
+    ref, A = oracle.energies(D, D["poses"], n_threads=-1, with_abs=True)
+    for v in ("ieee", "fast", "comp", "fp64"):
+        E = run(D, variant=v)
+        err = scaled_error(E, ref, A, v)
+        assert err.max() <= GATE[v], (v, err.max())
+
+
+def test_deterministic_repeat():
+    D = synth.make_deck(105, 20, 500, 34, 2048)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    a = bude.energies(deck, P).clone()
+    b = bude.energies(deck, P).clone()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+# --- edge cases -----------------------------------------------------------
+
+def test_zero_poses_is_noop():
+    D = synth.make_deck(106, 4, 50, 5, 0)
+    deck = bude.Deck(D, device=DEV)
+    E = bude.energies(deck, torch.zeros((6, 0), device=DEV))
+    assert E.numel() == 0
+
+
+@pytest.mark.parametrize("which", ["lig", "pro"])
+def test_empty_molecule_gives_zero(which):
+    D = synth.make_deck(107, 5, 60, 6, 70)
+    if which == "lig":
+        D["lig_xyz"] = D["lig_xyz"][:0]
+        D["lig_type"] = D["lig_type"][:0]
+    else:
+        D["pro_xyz"] = D["pro_xyz"][:0]
+        D["pro_type"] = D["pro_type"][:0]
+    E = run(D)
+    assert np.all(E == 0.0)
+
+
+def test_single_pose_single_pair_closed_form():
+    # one ligand atom at the origin, one protein atom at 2 A: types A and B of
+    # the hand-worked table give E = 1/9
+    D = dict(lig_xyz=np.zeros((1, 3), np.float32), lig_type=np.array([0], np.int32),
+             pro_xyz=np.array([[2.0, 0, 0]], np.float32), pro_type=np.array([1], np.int32),
+             radius=np.array([1.5, 1.5], np.float32), hardness=np.array([10, 30], np.float32),
+             elsc=np.array([0.5, -0.5], np.float32), hbtype=np.array([1, 2], np.int32),
+             poses=np.zeros((6, 1), np.float32))
+    # e = 20/9 - 2 cancels: compare at the scale A = (20/9 + 2)/2 of the terms
+    A = (20.0 / 9.0 + 2.0) / 2.0
+    for v in ("ieee", "fast", "comp", "fp64"):
+        E = run(D, variant=v)
+        assert abs(E[0] - 1.0 / 9.0) <= GATE[v] * A + (2.0 ** -24 if v == "fp64" else 0.0)
+
+
+def test_atom_on_atom_is_finite():
+    D = synth.make_deck(108, 6, 80, 7, 40)
+    D["pro_xyz"][5] = D["lig_xyz"][2]          # exact overlap at the identity pose
+    P = np.zeros((6, 40), np.float32)
+    P[3:, 1:] = D["poses"][3:, 1:]
+    E, ref, A = check(D, "ieee", poses=P)
+    assert np.isfinite(E).all()
+    check(D, "fast", poses=P)
+    check(D, "fp64", poses=P)
+
+
+def test_nan_pose_gives_nan_and_far_pose_gives_zero():
+    D = synth.make_deck(109, 6, 80, 7, 64)
+    P = D["poses"].copy()
+    P[0, 3] = np.nan
+    P[4, 7] = np.nan
+    P[1, 9] = np.inf
+    P[3, 11] = np.inf        # infinitely far ligand: every pair beyond the cutoff
+    P[3, 12] = 1e6
+    ref = oracle.energies(D, P)
+    for v in ("ieee", "fast", "comp", "fp64"):
+        E = run(D, P, v)
+        assert np.isnan(E[[3, 7, 9]]).all()
+        assert E[11] == 0.0 and E[12] == 0.0
+        ok = np.isfinite(ref)
+        np.testing.assert_array_equal(np.isnan(E), ~ok)
+
+
+def test_type_indexing_is_exact_with_many_types():
+    # FP64 on the GPU matches to 1e-12: any wrong type lookup would be gross
+    D = synth.make_deck(110, 40, 400, 64, 256)
+    E, ref, A = check(D, "fp64")
+    check(D, "ieee")
+    # and every ligand type maps to its own table row
+    deck = bude.Deck(D, device=DEV)
+    assert deck.n_rows == len(np.unique(D["lig_type"]))
+
+
+def test_pair_table_too_large_is_a_clean_error():
+    # 60 ligand rows x 600 types of 32-byte records cannot be staged
+    D = synth.make_deck(116, 200, 300, 600, 64)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    with pytest.raises(bude.BudeError) as e:
+        bude.energies(deck, P)
+    assert e.value.code == bude.ERR_UNSUPPORTED
+    # the device is still healthy afterwards
+    D2 = synth.make_deck(117, 5, 50, 6, 32)
+    check(D2, "ieee")
+
+
+def test_invalid_decks_are_rejected():
+    D = synth.make_deck(111, 5, 50, 6, 8)
+    bad = dict(D, pro_type=D["pro_type"].copy())
+    bad["pro_type"][7] = 6
+    with pytest.raises(bude.BudeError) as e:
+        bude.Deck(bad, device=DEV)
+    assert e.value.code == bude.ERR_INVALID_ARG
+    bad = dict(D, lig_type=D["lig_type"].copy())
+    bad["lig_type"][0] = -1
+    with pytest.raises(bude.BudeError):
+        bude.Deck(bad, device=DEV)
+    bad = dict(D, radius=D["radius"].copy())
+    bad["radius"][2] = 0.0
+    with pytest.raises(bude.BudeError):
+        bude.Deck(bad, device=DEV)
+    bad = dict(D, hbtype=D["hbtype"].copy())
+    bad["hbtype"][1] = 3
+    with pytest.raises(bude.BudeError):
+        bude.Deck(bad, device=DEV)
+    bad = dict(D, pro_xyz=D["pro_xyz"].copy())
+    bad["pro_xyz"][3, 1] = np.nan
+    with pytest.raises(bude.BudeError):
+        bude.Deck(bad, device=DEV)
+
+
+def test_bad_options_are_rejected():
+    D = synth.make_deck(112, 5, 50, 6, 8)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    for kw in (dict(ppwi=3), dict(block=48), dict(block=2048), dict(variant=7),
+               dict(variant="fp64", ppwi=8), dict(tile=-1)):
+        with pytest.raises(bude.BudeError):
+            bude.energies(deck, P, **kw)
+
+
+# --- full-size workload: every pose computed, a sample checked --------------
+
+def test_full_size_sampled_against_oracle():
+    D = synth.make_deck(1, **synth.FULL)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(D["poses"].shape[1], 48, replace=False))
+    idx[-1] = D["poses"].shape[1] - 1
+    ref, A = oracle.energies(D, D["poses"][:, idx], n_threads=-1, with_abs=True)
+    for v in ("ieee", "fast", "comp"):
+        E = bude.energies(deck, P, variant=v).cpu().numpy()
+        assert np.isfinite(E).all()
+        err = scaled_error(E[idx], ref, A)
+        assert err.max() <= GATE[v], (v, err.max())
+
+
+# --- batched --------------------------------------------------------------
+
+def test_batched_uneven_against_oracle_and_plain():
+    shapes = [(8, 500, 300), (3, 40, 1), (17, 1200, 1025), (5, 77, 33), (1, 1, 7),
+              (30, 640, 4097)]
+    decks_np = [synth.make_deck([7, i], nl, npro, 34, n) for i, (nl, npro, n) in enumerate(shapes)]
+    decks = [bude.Deck(d, device=DEV) for d in decks_np]
+    poses = [torch.from_numpy(d["poses"]).to(DEV) for d in decks_np]
+    outs = bude.energies_batched(decks, poses)
+    outs2 = bude.energies_batched(decks, poses)    # graph replay
+    torch.cuda.synchronize()
+    for d, p, o, o2, dnp in zip(decks, poses, outs, outs2, decks_np):
+        assert torch.equal(o, o2)
+        n = dnp["poses"].shape[1]
+        idx = np.unique(np.linspace(0, n - 1, min(n, 40)).astype(int))
+        ref, A = oracle.energies(dnp, dnp["poses"][:, idx], n_threads=-1, with_abs=True)
+        E = o.cpu().numpy()
+        assert scaled_error(E[idx], ref, A).max() <= GATE["ieee"]
+        plain = bude.energies(d, p).cpu().numpy()
+        assert scaled_error(E, plain.astype(np.float64), np.abs(plain)).max() <= 2 * GATE["ieee"]
+
+
+def test_batched_with_empty_instances():
+    d0 = synth.make_deck(113, 6, 90, 8, 50)
+    d1 = synth.make_deck(114, 6, 90, 8, 0)
+    d2 = synth.make_deck(115, 6, 90, 8, 20)
+    d2["lig_xyz"], d2["lig_type"] = d2["lig_xyz"][:0], d2["lig_type"][:0]
+    decks = [bude.Deck(d, device=DEV) for d in (d0, d1, d2)]
+    poses = [torch.from_numpy(d["poses"]).to(DEV) for d in (d0, d1, d2)]
+    outs = [torch.full((p.shape[1],), 7.0, device=DEV) for p in poses]
+    bude.energies_batched(decks, poses, outs)
+    torch.cuda.synchronize()
+    assert torch.all(outs[2] == 0)
+    ref, A = oracle.energies(d0, d0["poses"], with_abs=True)
+    assert scaled_error(outs[0].cpu().numpy(), ref, A).max() <= GATE["ieee"]
+
+
+# --- adjoint --------------------------------------------------------------
+
+GRAD_GATE = {"ieee": 1e-4, "fast": 1e-4, "comp": 1e-4, "fp64": 1e-10}
+
+
+def grad_error(G, Gref, S, variant=None):
+    G = np.asarray(G, np.float64)
+    d = np.abs(G - Gref)
+    if variant == "fp64":
+        d = np.maximum(d - np.abs(Gref) * 2.0 ** -24 * (1 + 1e-9), 0.0)
+    sa = np.maximum(S[0], 1.0)
+    st = np.maximum(S[1], 1.0)
+    return max(np.max(d[:3] / sa), np.max(d[3:] / st))
+
+
+@pytest.mark.parametrize("variant", ["ieee", "fast", "comp", "fp64"])
+def test_pose_gradient_against_oracle(variant):
+    D = synth.make_deck(120, 12, 300, 34, 700)
+    Eref, Gref, S = oracle.pose_grad(D, D["poses"], n_threads=-1, with_scale=True)
+    _, A = oracle.energies(D, D["poses"], n_threads=-1, with_abs=True)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    E, G = bude.pose_grad(deck, P, variant=variant)
+    torch.cuda.synchronize()
+    assert scaled_error(E.cpu().numpy(), Eref, A, variant).max() <= GATE[variant]
+    assert grad_error(G.cpu().numpy(), Gref, S, variant) <= GRAD_GATE[variant]
+
+
+@pytest.mark.parametrize("ppwi", [1, 2, 4, 8])
+def test_pose_gradient_launch_shapes(ppwi):
+    D = synth.make_deck(121, 7, 210, 34, 333)
+    Eref, Gref, S = oracle.pose_grad(D, D["poses"], n_threads=-1, with_scale=True)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    _, G = bude.pose_grad(deck, P, want_energy=False, ppwi=ppwi, block=128, tile=64)
+    assert grad_error(G.cpu().numpy(), Gref, S) <= GRAD_GATE["ieee"]
+
+
+def test_pose_gradient_matches_central_differences_of_gpu_fp64():
+    D = synth.make_deck(122, 8, 200, 34, 64)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    _, G = bude.pose_grad(deck, P, variant="fp64")
+    _, _, S = oracle.pose_grad(D, D["poses"], with_scale=True)
+    h = 1e-3   # float32 poses: the step must be representable around |pose| <= 5
+    G = G.cpu().numpy().astype(np.float64)
+    for j in range(6):
+        Pp, Pm = D["poses"].copy(), D["poses"].copy()
+        Pp[j] += np.float32(h)
+        Pm[j] -= np.float32(h)
+        step = (Pp[j].astype(np.float64) - Pm[j].astype(np.float64))
+        fd = (run(D, Pp, "fp64").astype(np.float64) - run(D, Pm, "fp64").astype(np.float64)) / step
+        scale = np.maximum(S[0] if j < 3 else S[1], 1.0)
+        assert np.median(np.abs(fd - G[j]) / scale) < 1e-3, j
+
+
+def test_gradient_full_size_sampled():
+    D = synth.make_deck(4, **synth.GRAD)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    E, G = bude.pose_grad(deck, P)
+    idx = np.sort(np.random.default_rng(1).choice(P.shape[1], 24, replace=False))
+    Eref, Gref, S = oracle.pose_grad(D, D["poses"][:, idx], n_threads=-1, with_scale=True)
+    _, A = oracle.energies(D, D["poses"][:, idx], n_threads=-1, with_abs=True)
+    assert scaled_error(E.cpu().numpy()[idx], Eref, A).max() <= GATE["ieee"]
+    assert grad_error(G.cpu().numpy()[:, idx], Gref, S) <= GRAD_GATE["ieee"]
+
+
+def test_autograd_function_and_refinement():
+    D = synth.make_deck(123, 10, 400, 34, 256)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV).requires_grad_(True)
+    E = bude.PoseEnergy.apply(P, deck, None)
+    w = torch.linspace(0.5, 1.5, E.numel(), device=DEV)
+    (E * w).sum().backward()
+    _, G = bude.pose_grad(deck, P.detach())
+    torch.testing.assert_close(P.grad, G * w.unsqueeze(0))
+    p2, hist = bude.refine(deck, P.detach(), steps=10, lr=1e-3)
+    # gradient descent with a small step lowers the mean energy
+    assert hist[-1].mean().item() < hist[0].mean().item()
