@@ -133,6 +133,68 @@ def cpu_baseline_leg(deck, n_poses_total, budget_s=12.0, threads=-1):
     return n / dt, n, dt, cores, E, A
 
 
+def batched_vs_plain(bude, synth, tune, dev, timed, variant="fast", count=64, seed=3):
+    """64 uneven decks: one persistent graph-replayed launch vs 64 plain launches."""
+    import torch
+    decks_np = synth.make_batched(seed, count)
+    decks = [bude.Deck(d, device=dev) for d in decks_np]
+    poses = [torch.from_numpy(d["poses"]).to(dev) for d in decks_np]
+    outs_b = [torch.empty(p.shape[1], dtype=torch.float32, device=dev) for p in poses]
+    outs_p = [torch.empty(p.shape[1], dtype=torch.float32, device=dev) for p in poses]
+    t = tune.load_table()
+    e = t.get(tune.key(variant, f"n{count}", "batched"))
+    if e:
+        ob = bude.LaunchOptions(variant=variant, ppwi=e["ppwi"], block=e["block"],
+                                ctas_per_sm=e["ctas_per_sm"], tile=e["tile"])
+    else:
+        ob = bude.default_options(variant)
+    op = bude.default_options(variant)
+
+    def run_batched():
+        bude.energies_batched(decks, poses, outs_b, opts=ob)
+
+    def run_plain():
+        n = 0
+        for d, p, o in zip(decks, poses, outs_p):
+            bude.energies(d, p, out=o, opts=op)
+            n += bude.launch_count()
+        plain_launches[0] = n
+
+    plain_launches = [0]
+
+    ms_b, lb = timed(run_batched, 10, 3)
+    ms_p, lp = timed(run_plain, 10, 3)
+    pairs = sum(len(d["lig_type"]) * len(d["pro_type"]) * d["poses"].shape[1] for d in decks_np)
+    n = sum(d["poses"].shape[1] for d in decks_np)
+    diff = max(float(((a - b).abs() / b.abs().clamp_min(1.0)).max()) for a, b in zip(outs_b, outs_p))
+    for d in decks:
+        d.close()
+    tb, tp = statistics.mean(ms_b), statistics.mean(ms_p)
+    return {"workload": f"{count} decks, log-uniform lig 8-128, pro 500-5000, poses 1024-65536, seed {seed}",
+            "variant": variant, "poses": n, "pair_evaluations": pairs,
+            "batched_ms": tb, "plain_ms": tp, "speedup": tp / tb,
+            "batched_poses_per_s": n / (tb / 1e3), "plain_poses_per_s": n / (tp / 1e3),
+            "batched_launches": lb // 10, "plain_launches": plain_launches[0],
+            "batched_opts": {"ppwi": ob.ppwi, "block": ob.block, "ctas_per_sm": ob.ctas_per_sm},
+            "max_rel_diff_batched_vs_plain": diff}
+
+
+def adjoint_throughput(bude, synth, tune, dev, timed, variant="fast"):
+    """Energies + pose gradients of 16384 poses on the 64 x 2672 deck."""
+    import torch
+    D = synth.make_deck(4, **synth.GRAD)
+    deck = bude.Deck(D, device=dev)
+    P = torch.from_numpy(D["poses"]).to(dev)
+    o = tune.lookup(variant, 64, 2672, D["poses"].shape[1], mode="grad") or \
+        bude.LaunchOptions(variant=variant)
+    ms, _ = timed(lambda: bude.pose_grad(deck, P, opts=o), 10, 3)
+    deck.close()
+    t = statistics.mean(ms)
+    return {"workload": "64 lig x 2672 pro x 16384 poses, seed 4", "variant": variant,
+            "ms": t, "poses_per_s": P.shape[1] / (t / 1e3),
+            "opts": {"ppwi": o.ppwi, "block": o.block, "ctas_per_sm": o.ctas_per_sm}}
+
+
 def reference_arm(args):
     """The FP64 oracle as it stands, timed on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -172,7 +234,7 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variant", default="fast", choices=["ieee", "fast", "comp"])
@@ -188,7 +250,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2509_21039_gb300 import bude, synth
+    from paper_2509_21039_gb300 import bude, synth, tune
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -213,8 +275,10 @@ def main():
     out = torch.empty(n, dtype=torch.float32, device=dev)
     flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    opts = bude.LaunchOptions(variant=args.variant)
+    # launch shapes found by the autotuner on GB300 (tuned.json), else defaults
+    tune.apply(n_lig=FULL["n_lig"], n_pro=FULL["n_pro"], n_poses=FULL["n_poses"])
     resolved = bude.default_options(args.variant)
+    opts = resolved
 
     def step():
         bude.energies(deck, poses, out=out, opts=opts)
@@ -312,6 +376,10 @@ def main():
         "roofline": roofline,
         "clocks": clocks,
     }
+
+    if not args.no_extras:
+        line["batched"] = batched_vs_plain(bude, synth, tune, dev, timed)
+        line["adjoint"] = adjoint_throughput(bude, synth, tune, dev, timed)
 
     # CPU-baseline leg: the FP64 oracle on a bounded sample of the same poses.
     # Its sample energies also give each variant's error on that sample.

@@ -2,7 +2,7 @@
  * bude.h -- C ABI of the GB300 (sm_103a) pose-energy library libbude.so.
  *
  * The library evaluates the per-pose protein-ligand docking energy that the
- * miniBUDE "fasten" kernel computes (arxiv 2509.21039, Sec. 3, Listing 4; FLOP
+ * miniBUDE "fasten" kernel computes (arxiv 2509.21039, Sec. 2.2, Listing 4; FLOP
  * count Eq. 3): every pose moves the ligand rigidly (three angles, three
  * translations), every ligand x protein atom pair is scored by steric,
  * electrostatic and desolvation terms looked up by atom-type pair, and half
@@ -64,7 +64,7 @@ extern "C" {
 /*
  * Deck description: the three inputs of Listing 4 besides the poses.
  * Atom records are 16 bytes, {x, y, z, type}, the type being an int32 stored
- * in the fourth 4-byte word (Sec. 3 describes the same flattening of the
+ * in the fourth 4-byte word (Sec. 2.2 describes the same flattening of the
  * Atom struct to four 4-byte fields).  Forcefield rows are
  * {radius, hardness, elsc, hbtype} with hbtype an int32 in the fourth word
  * (0 none, 1 donor, 2 acceptor).
@@ -163,6 +163,17 @@ BUDE_API int bude_energies_batched(bude_deck* const* decks, const float* const* 
 BUDE_API int bude_pose_grad(bude_deck* deck, const float* poses, int64_t n,
                    float* energies, float* grad, const bude_options* opts,
                    void* stream);
+
+/*
+ * bude_selfcheck_sqrt -- diagnostics for the BUDE_FP32_IEEE energy kernels,
+ * whose square root is computed without branches (Markstein's FMA
+ * correction of an approximate reciprocal root).  Compares it bit for bit
+ * with the correctly rounded sqrt over every float in [2^-100, 2^128) (the
+ * kernels add 2^-100 to each squared distance) and stores the
+ * number of mismatches (0 expected) and the smallest mismatching bit pattern
+ * (0xffffffff when none).  Synchronises "stream".
+ */
+BUDE_API int bude_selfcheck_sqrt(uint64_t* mismatches, uint32_t* first_bad, void* stream);
 
 /* Default options the library uses for a variant when a field is zero. */
 BUDE_API int bude_get_default_options(int32_t variant, bude_options* out);

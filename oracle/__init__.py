@@ -1,4 +1,4 @@
-"""FP64 CPU oracle for the miniBUDE pose energy (arxiv 2509.21039, Sec. 3,
+"""FP64 CPU oracle for the miniBUDE pose energy (arxiv 2509.21039, Sec. 2.2,
 Listing 4, Eq. 3) -- TEST INFRASTRUCTURE ONLY.
 
 Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of

@@ -1,6 +1,6 @@
 /*
  * FP64 CPU oracle for the per-pose protein-ligand docking energy (miniBUDE
- * "fasten", arxiv 2509.21039 Sec. 3, Listing 4 and Eq. 3).
+ * "fasten", arxiv 2509.21039 Sec. 2.2, Listing 4; FLOP count Eq. 3).
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
  * reference the CUDA path is checked against.  Only the test suite, the smoke
@@ -19,8 +19,9 @@
  * element is cos(a1)*cos(a2) as in Listing 4; the product Rz*Ry*Rx is the
  * reading that gives it (pinned by basis-vector tests).
  *
- * The paper names the steric, electrostatic and desolvation terms but never
- * writes them down, so the pair energy e(a, b, d) is this project's own
+ * The paper describes fasten as scoring how strongly two molecules interact
+ * (Sec. 2.2) but prints no forcefield, so the pair energy e(a, b, d) -- a
+ * steric, an electrostatic and a desolvation term -- is this project's own
  * definition, built only from the per-type parameters radius r, hardness h,
  * charge-like q and hydrogen-bond class hb (0 none, 1 donor, 2 acceptor):
  *

@@ -1,4 +1,4 @@
-"""GB300-native miniBUDE pose-energy engine (arxiv 2509.21039, Sec. 3).
+"""GB300-native miniBUDE pose-energy engine (arxiv 2509.21039, Sec. 2.2, Listing 4).
 
 The compute path is the C-ABI library ``libbude.so`` built from ``csrc/``;
 ``paper_2509_21039_gb300.bude`` is its thin ctypes binding.  ``synth`` draws

@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         "bude_get_default_options": (ci, [i32, ctypes.POINTER(Options)]),
         "bude_set_default_options": (ci, [ctypes.POINTER(Options)]),
         "bude_last_launch_count": (i64, []),
+        "bude_selfcheck_sqrt": (ci, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32), vp]),
         "bude_status_string": (ctypes.c_char_p, [ci]),
         "bude_last_error": (ctypes.c_char_p, []),
     }
@@ -108,6 +109,15 @@ def _check(rc: int):
 def _stream_ptr(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def selfcheck_sqrt(stream=None):
+    """(mismatches, first mismatching bits) of the IEEE kernels' square root
+    against sqrt.rn over every normal float."""
+    n = ctypes.c_uint64()
+    first = ctypes.c_uint32()
+    _check(load().bude_selfcheck_sqrt(ctypes.byref(n), ctypes.byref(first), _stream_ptr(stream)))
+    return n.value, first.value
 
 
 def launch_count() -> int:

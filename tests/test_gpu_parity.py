@@ -365,3 +365,8 @@ def test_autograd_function_and_refinement():
     p2, hist = bude.refine(deck, P.detach(), steps=10, lr=1e-3)
     # gradient descent with a small step lowers the mean energy
     assert hist[-1].mean().item() < hist[0].mean().item()
+
+
+def test_ieee_square_root_is_correctly_rounded_everywhere():
+    mism, first = bude.selfcheck_sqrt()
+    assert mism == 0, f"{mism} mismatches, first at bits {first:#010x}"
