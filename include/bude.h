@@ -152,6 +152,35 @@ BUDE_API int bude_energies_batched(bude_deck* const* decks, const float* const* 
                           int32_t count, const bude_options* opts, void* stream);
 
 /*
+ * bude_energies_noalloc -- bude_energies for callers that must not allocate
+ * device memory.  (The paper has no counterpart: this is a deployment
+ * variant.)
+ *
+ * Some hosts own the whole device-memory budget and forbid allocation inside
+ * their execution callbacks (plugins of inference servers and of other
+ * frameworks with their own allocators), and latency-critical loops cannot
+ * afford cudaMalloc's implicit synchronisation.  This call runs the same
+ * kernel as bude_energies but keeps the kernel's scratch (cross-CTA partial
+ * sums and arrival tickets) in one fixed array that the library declares in
+ * device memory: 4 MiB of partial sums plus 64 KiB of tickets, held by every
+ * GPU that loads the library until the process exits.  It calls no
+ * cudaMalloc or cudaFree and no allocating routine; it clears the tickets
+ * with cudaMemsetAsync and launches on "stream".
+ *
+ * Limits: a call needs (CTAs of the grid + pose tiles) x 32 x ppwi partial
+ * sums and one ticket per pose tile of 32 x ppwi poses; with the tuned
+ * shapes that is a few hundred thousand poses per call.  Larger calls return
+ * BUDE_ERR_UNSUPPORTED with the sizes in bude_last_error().
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array, so calls whose kernels overlap
+ * on the GPU (different streams, or different threads) race and must be
+ * serialised by the caller.  Arguments and results are as bude_energies.
+ */
+BUDE_API int bude_energies_noalloc(bude_deck* deck, const float* poses, int64_t n,
+                                   float* energies, const bude_options* opts, void* stream);
+
+/*
  * bude_pose_grad -- energies and their gradient with respect to the six pose
  * parameters (the adjoint of bude_energies).
  *

@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
         "bude_deck_info": (ci, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                 ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "bude_energies": (ci, [vp, vp, i64, vp, ctypes.POINTER(Options), vp]),
+        "bude_energies_noalloc": (ci, [vp, vp, i64, vp, ctypes.POINTER(Options), vp]),
         "bude_energies_batched": (ci, [ctypes.POINTER(vp), ctypes.POINTER(vp),
                                        ctypes.POINTER(i64), ctypes.POINTER(vp), i32,
                                        ctypes.POINTER(Options), vp]),
@@ -245,6 +246,22 @@ def energies(deck: Deck, poses: torch.Tensor, out: torch.Tensor | None = None,
     rc = load().bude_energies(deck.handle, ctypes.c_void_p(poses.data_ptr()), n,
                               ctypes.c_void_p(out.data_ptr()), ctypes.byref(o),
                               _stream_ptr(stream))
+    _check(rc)
+    return out
+
+
+def energies_noalloc(deck: Deck, poses: torch.Tensor, out: torch.Tensor,
+                     opts=None, stream=None, **kw) -> torch.Tensor:
+    """bude_energies_noalloc: energies into a caller-provided ``out`` with the
+    kernel's scratch in the library's fixed device array (no allocation)."""
+    _check_poses(poses, deck)
+    n = poses.shape[1]
+    if out.shape != (n,) or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 [n] tensor")
+    o = _opts(opts, **kw)
+    rc = load().bude_energies_noalloc(deck.handle, ctypes.c_void_p(poses.data_ptr()), n,
+                                      ctypes.c_void_p(out.data_ptr()), ctypes.byref(o),
+                                      _stream_ptr(stream))
     _check(rc)
     return out
 

@@ -668,3 +668,84 @@ int bude_energies_batched(bude_deck* const* decks, const float* const* poses, co
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free energies: the same persistent kernel as bude_energies, with
+// its cross-CTA partial sums and arrival tickets in a fixed device array
+// that lives as long as the library is loaded.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticPartialDoubles = 512u * 1024u;  // 4 MiB of partial sums
+constexpr size_t kStaticTickets = 16u * 1024u;          // 64 KiB of arrival tickets
+
+struct StaticScratch {
+    double partial[kStaticPartialDoubles];
+    unsigned counter[kStaticTickets];
+};
+
+// Held by every GPU that loads libbude.so, from load until process exit.
+static __device__ __align__(256) StaticScratch g_static_scratch;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+StaticScratch* g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device, looked up once
+// per device (the host-side symbol is only a stand-in, not a device address).
+int static_scratch(int dev, StaticScratch** out)
+{
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(BUDE_ERR_UNSUPPORTED, "device ordinal %d above %d", dev, kMaxDevices - 1);
+    std::lock_guard<std::mutex> lk(g_static_mutex);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_static_scratch), "cudaGetSymbolAddress");
+        g_static_ptr[dev] = static_cast<StaticScratch*>(p);
+    }
+    *out = g_static_ptr[dev];
+    return BUDE_OK;
+}
+
+}  // namespace
+
+extern "C" BUDE_API int bude_energies_noalloc(bude_deck* deck, const float* poses, int64_t n,
+                                              float* energies, const bude_options* opts,
+                                              void* stream)
+{
+    g_launches = 0;
+    if (!deck) return fail(BUDE_ERR_INVALID_ARG, "deck is NULL");
+    if (n < 0) return fail(BUDE_ERR_INVALID_ARG, "n = %lld < 0", (long long)n);
+    if (n == 0) return BUDE_OK;
+    if (!poses || !energies) return fail(BUDE_ERR_INVALID_ARG, "poses or energies is NULL");
+    Resolved r;
+    int rc = resolve_options(opts, false, &r);
+    if (rc) return rc;
+    int dev;
+    if ((rc = current_device(&dev))) return rc;
+    if (dev != deck->device)
+        return fail(BUDE_ERR_INVALID_ARG, "deck lives on device %d, current device is %d",
+                    deck->device, dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((long long)deck->n_lig * deck->n_pro == 0) {
+        CK(cudaMemsetAsync(energies, 0, (size_t)n * sizeof(float), s), "memset");
+        return BUDE_OK;
+    }
+    Plan pl;
+    rc = make_plan({deck}, {poses}, {(long long)n}, {energies}, {nullptr}, r, false, dev, &pl);
+    if (rc) return rc;
+    const size_t need_doubles = partial_bytes_for(pl, r, false) / sizeof(double);
+    if (need_doubles > kStaticPartialDoubles || (size_t)pl.n_tiles > kStaticTickets)
+        return fail(BUDE_ERR_UNSUPPORTED,
+                    "bude_energies_noalloc: %lld poses need %zu partial sums and %lld tickets; "
+                    "its fixed scratch holds %zu and %zu (use fewer poses per call, or "
+                    "bude_energies)",
+                    (long long)n, need_doubles, pl.n_tiles, kStaticPartialDoubles,
+                    kStaticTickets);
+    StaticScratch* sc = nullptr;
+    if ((rc = static_scratch(dev, &sc))) return rc;
+    // tickets must start at zero; the partial sums are written before read
+    CK(cudaMemsetAsync(sc->counter, 0, (size_t)pl.n_tiles * sizeof(unsigned), s),
+       "ticket clear");
+    return launch_plan(pl, r, nullptr, sc->partial, sc->counter, s);
+}
