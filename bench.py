@@ -206,7 +206,7 @@ def reference_arm(args):
     D = synth.make_deck(1, **FULL)
     cores = oracle.max_threads()
     # per step: a bounded sample of the poses, sized so the whole run stays short
-    per_step = max(cores, 16)
+    per_step = max(4 * cores, 64)
     for _ in range(args.warmup):
         oracle.energies(D, D["poses"][:, :cores], n_threads=-1)
     times = []

@@ -259,9 +259,13 @@ int make_plan(const std::vector<const bude_deck*>& decks, const std::vector<cons
     int occ = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pl->fn, r.block, pl->smem),
        "occupancy query");
-    if (occ < 1)
-        return fail(BUDE_ERR_UNSUPPORTED, "block %d with %zu B shared memory cannot be resident",
-                    r.block, pl->smem);
+    if (occ < 1) {
+        cudaFuncAttributes fa;
+        int regs = cudaFuncGetAttributes(&fa, pl->fn) == cudaSuccess ? fa.numRegs : -1;
+        return fail(BUDE_ERR_UNSUPPORTED,
+                    "block %d cannot be resident: %d registers per thread, %zu B shared memory",
+                    r.block, regs, pl->smem);
+    }
     occ = std::min(occ, r.cps);
     long long grid = (long long)di.sms * occ;
     if (grid > pl->n_total) grid = pl->n_total;

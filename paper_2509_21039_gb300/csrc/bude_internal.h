@@ -6,7 +6,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
-#include "../../include/bude.h"
+#include "bude.h"
 #include "bude_kernels.cuh"
 
 namespace bude {
