@@ -111,12 +111,22 @@ const void* kernel_for(int variant, int P, bool G)
     return nullptr;
 }
 
-// Bytes of one type-pair record for a variant / mode.
-size_t record_bytes(int variant, bool G)
+// Packed FP32x2 kernels: FP32 energies with an even P (mirrors the kernel).
+bool packed(int variant, int P, bool G)
+{
+    return !G && variant != BUDE_FP64 && P % 2 == 0;
+}
+
+// Bytes of one type-pair record in shared memory for a variant / mode.
+size_t record_bytes(int variant, bool G, int P)
 {
     if (variant == BUDE_FP64) return sizeof(PairD);
-    return G ? sizeof(PairG) : sizeof(PairF);
+    if (G) return sizeof(PairG);
+    return packed(variant, P, G) ? 2 * sizeof(PairF) : sizeof(PairF);
 }
+
+// Bytes of one staged protein atom in shared memory.
+size_t protein_bytes(int variant, int P, bool G) { return packed(variant, P, G) ? 32 : 16; }
 
 // Dynamic shared memory of pose_kernel before the pair table and protein
 // chunk: max(transforms, warp partials) + final sums.  Mirrors the kernel.
@@ -182,9 +192,10 @@ struct InstanceShape {
 int chunk_for(const InstanceShape& s, const Resolved& r, bool G, size_t budget)
 {
     const size_t fixed = smem_fixed(r.variant, r.P, G, r.block);
-    const size_t table = (size_t)s.n_rows * s.n_types * record_bytes(r.variant, G);
-    if (fixed + table + 16 * 32 > budget) return -1;
-    size_t cap = (budget - fixed - table) / 16;
+    const size_t table = (size_t)s.n_rows * s.n_types * record_bytes(r.variant, G, r.P);
+    const size_t pb = protein_bytes(r.variant, r.P, G);
+    if (fixed + table + pb * 32 > budget) return -1;
+    size_t cap = (budget - fixed - table) / pb;
     int want = s.n_pro;
     if (r.tile > 0) want = std::min(want, r.tile);
     int ch = (int)std::min<size_t>((size_t)std::max(want, 1), cap);
@@ -244,8 +255,8 @@ int make_plan(const std::vector<const bude_deck*>& decks, const std::vector<cons
         k = I.k_end;
         tiles += nt;
         const size_t sm = smem_fixed(r.variant, r.P, G, r.block) +
-                          (size_t)d->n_rows * d->n_types * record_bytes(r.variant, G) +
-                          16 * (size_t)ch;
+                          (size_t)d->n_rows * d->n_types * record_bytes(r.variant, G, r.P) +
+                          protein_bytes(r.variant, r.P, G) * (size_t)ch;
         smem_max = std::max(smem_max, sm);
         pl->inst.push_back(I);
     }
