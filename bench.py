@@ -252,9 +252,8 @@ def main():
     import torch.distributed as dist
     from paper_2509_21039_gb300 import bude, synth, tune
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2509_21039_gb300 import dist as bdist
+    rank, local, world = bdist.world()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -268,7 +267,7 @@ def main():
     if args.poses:
         shape["n_poses"] = args.poses
     # each rank docks its own deck (independent problems: weak scaling)
-    D = synth.make_deck(1 + rank, **shape)
+    D = synth.make_deck(bdist.rank_seed(1, rank), **shape)
     deck = bude.Deck(D, device=dev)
     poses = torch.from_numpy(D["poses"]).to(dev)
     n = poses.shape[1]
@@ -309,12 +308,8 @@ def main():
     with ClockSampler(local, os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None) as clk:
         ms, launches = timed(step, args.steps, args.warmup)
-    ms_mean = statistics.mean(ms)
-    if world > 1:
-        t = torch.tensor([ms_mean], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_mean = float(t.item())
-    value = world * n / (ms_mean / 1e3)
+    ms_mean = bdist.max_over_ranks(statistics.mean(ms), dev)
+    value = bdist.aggregate_rate(n, ms_mean, world)
 
     # end to end through the public API: pinned host poses in, host energies out
     host_poses = torch.from_numpy(D["poses"]).pin_memory()
@@ -327,11 +322,7 @@ def main():
         host_out.copy_(out, non_blocking=True)
 
     e2e_ms, _ = timed(e2e_step, max(3, args.steps // 2), 2)
-    e2e_mean = statistics.mean(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_mean], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_mean = float(t.item())
+    e2e_mean = bdist.max_over_ranks(statistics.mean(e2e_ms), dev)
 
     if rank != 0:
         if world > 1:
@@ -370,7 +361,7 @@ def main():
                    "l2": f"flushed ({args.flush_mb} MiB write) before every timed step",
                    "parallelism": f"independent decks per GPU x{world}"},
         "gpu_launches": int(launches),
-        "e2e": {"value": world * n / (e2e_mean / 1e3), "unit": "poses/s",
+        "e2e": {"value": bdist.aggregate_rate(n, e2e_mean, world), "unit": "poses/s",
                 "h2d_bytes_per_step": int(host_poses.numel() * 4),
                 "d2h_bytes_per_step": int(host_out.numel() * 4)},
         "roofline": roofline,
