@@ -111,18 +111,19 @@ const void* kernel_for(int variant, int P, bool G)
     return nullptr;
 }
 
-// Packed FP32x2 kernels: FP32 energies with an even P (mirrors the kernel).
+// Packed FP32x2 kernels: FP32 variants with an even P (mirrors the kernel).
 bool packed(int variant, int P, bool G)
 {
-    return !G && variant != BUDE_FP64 && P % 2 == 0;
+    (void)G;
+    return variant != BUDE_FP64 && P % 2 == 0;
 }
 
 // Bytes of one type-pair record in shared memory for a variant / mode.
 size_t record_bytes(int variant, bool G, int P)
 {
     if (variant == BUDE_FP64) return sizeof(PairD);
-    if (G) return sizeof(PairG);
-    return packed(variant, P, G) ? 2 * sizeof(PairF) : sizeof(PairF);
+    if (packed(variant, P, G)) return G ? 96 : 64;
+    return G ? sizeof(PairG) : sizeof(PairF);
 }
 
 // Bytes of one staged protein atom in shared memory.
