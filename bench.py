@@ -195,6 +195,31 @@ def adjoint_throughput(bude, synth, tune, dev, timed, variant="fast"):
             "opts": {"ppwi": o.ppwi, "block": o.block, "ctas_per_sm": o.ctas_per_sm}}
 
 
+def refine_throughput(bude, synth, tune, dev, timed, variant="fast", steps=10):
+    """Ten refinement steps on 16384 poses of the 64 x 2672 deck, one graph."""
+    import torch
+    D = synth.make_deck(4, **synth.GRAD)
+    deck = bude.Deck(D, device=dev)
+    P0 = torch.from_numpy(D["poses"]).to(dev)
+    P = P0.clone()
+    E = torch.empty(P.shape[1], device=dev)
+    o = tune.lookup(variant, 64, 2672, D["poses"].shape[1], mode="grad") or \
+        bude.LaunchOptions(variant=variant)
+    e0 = bude.energies(deck, P0).mean().item()
+
+    def step():
+        P.copy_(P0)
+        bude.refine_device(deck, P, steps=steps, step0=0.05, energies=E, opts=o)
+
+    ms, launches = timed(step, 5, 2)
+    deck.close()
+    t = statistics.mean(ms)
+    return {"workload": f"{steps} steps x 16384 poses, 64 lig x 2672 pro, seed 4",
+            "variant": variant, "ms": t, "pose_steps_per_s": steps * P.shape[1] / (t / 1e3),
+            "graph_launches_per_call": 1, "kernels_per_call": launches // 5,
+            "mean_energy_before": e0, "mean_energy_after": E.mean().item()}
+
+
 def reference_arm(args):
     """The FP64 oracle as it stands, timed on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -371,6 +396,7 @@ def main():
     if not args.no_extras:
         line["batched"] = batched_vs_plain(bude, synth, tune, dev, timed)
         line["adjoint"] = adjoint_throughput(bude, synth, tune, dev, timed)
+        line["refine"] = refine_throughput(bude, synth, tune, dev, timed)
 
     # CPU-baseline leg: the FP64 oracle on a bounded sample of the same poses.
     # Its sample energies also give each variant's error on that sample.

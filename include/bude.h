@@ -204,6 +204,27 @@ BUDE_API int bude_pose_grad(bude_deck* deck, const float* poses, int64_t n,
  */
 BUDE_API int bude_selfcheck_sqrt(uint64_t* mismatches, uint32_t* first_bad, void* stream);
 
+/*
+ * bude_refine -- on-device pose refinement (the docking step that follows
+ * scoring; the paper's Sec. 2.2 describes docking but benchmarks only the
+ * energy).  Per pose, "steps" iterations of normalised gradient descent with
+ * an adaptive step:
+ *   start:  E, g = energy and pose gradient at p;  alpha = step0
+ *   step:   p' = p - alpha g / |g|   (p' = p when |g| is 0 or not finite)
+ *           E', g' at p' (the adjoint kernel)
+ *           if E' < E: p, E, g = p', E', g' and alpha *= 1.25, else alpha *= 0.5
+ * so no pose's energy ever increases.  poses (device float32 [6][n]) is
+ * updated in place; energies (device float32 [n]) receives the final E.
+ * step0 is in pose units (radians and Angstrom share one step length).
+ * The first call with a given argument set allocates the plan's buffers
+ * (22 floats per pose) and captures the whole loop -- 2 + 3 x steps kernel
+ * launches -- into one CUDA graph; later calls replay it.  Uses the deck's
+ * workspace: calls on one deck must not overlap.  Variants and options as
+ * bude_pose_grad.
+ */
+BUDE_API int bude_refine(bude_deck* deck, float* poses, int64_t n, int32_t steps, float step0,
+                         float* energies, const bude_options* opts, void* stream);
+
 /* Default options the library uses for a variant when a field is zero. */
 BUDE_API int bude_get_default_options(int32_t variant, bude_options* out);
 BUDE_API int bude_set_default_options(const bude_options* opts);

@@ -162,3 +162,36 @@ def pose_grad(deck, poses, n_threads: int = 0, with_scale: bool = False):
     if rc != 0:
         raise ValueError("oracle_pose_grad rejected the deck")
     return (E, G, S) if with_scale else (E, G)
+
+
+# --- pose refinement (the docking step after scoring) ----------------------
+
+def refine(deck, poses, steps: int, step0: float, grow: float = 1.25, shrink: float = 0.5,
+           n_threads: int = 0):
+    """Per-pose normalised gradient descent with an adaptive step, in FP64.
+
+    The rule both the oracle and the CUDA path follow (this project's reading
+    of the refinement that docking performs after scoring; the paper stops at
+    the energy):
+      start: E, g = energy and pose gradient at p; alpha = step0
+      each step:  if |g| > 0:  p' = p - alpha g / |g|, else p' = p
+                  E', g' at p'
+                  if E' < E:  p, E, g = p', E', g';  alpha *= grow
+                  else:       alpha *= shrink
+    Returns (poses [6][n], energies [n], alpha [n]).
+    """
+    P = np.array(poses, dtype=np.float64).reshape(6, -1)
+    E, G = pose_grad(deck, P, n_threads=n_threads)
+    alpha = np.full(P.shape[1], float(step0))
+    for _ in range(steps):
+        norm = np.sqrt((G * G).sum(axis=0))
+        move = norm > 0
+        T = P.copy()
+        T[:, move] = P[:, move] - alpha[move] * G[:, move] / norm[move]
+        Et, Gt = pose_grad(deck, T, n_threads=n_threads)
+        acc = Et < E
+        P[:, acc] = T[:, acc]
+        E[acc] = Et[acc]
+        G[:, acc] = Gt[:, acc]
+        alpha = np.where(acc, alpha * grow, alpha * shrink)
+    return P, E, alpha

@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
                                        ctypes.POINTER(i64), ctypes.POINTER(vp), i32,
                                        ctypes.POINTER(Options), vp]),
         "bude_pose_grad": (ci, [vp, vp, i64, vp, vp, ctypes.POINTER(Options), vp]),
+        "bude_refine": (ci, [vp, vp, i64, i32, ctypes.c_float, vp, ctypes.POINTER(Options), vp]),
         "bude_get_default_options": (ci, [i32, ctypes.POINTER(Options)]),
         "bude_set_default_options": (ci, [ctypes.POINTER(Options)]),
         "bude_last_launch_count": (i64, []),
@@ -300,6 +301,23 @@ def pose_grad(deck: Deck, poses: torch.Tensor, want_energy: bool = True, opts=No
                                _stream_ptr(stream))
     _check(rc)
     return E, G
+
+
+def refine_device(deck: Deck, poses: torch.Tensor, steps: int = 10, step0: float = 0.1,
+                  energies: torch.Tensor | None = None, opts=None, stream=None, **kw):
+    """bude_refine: ``steps`` iterations of per-pose adaptive gradient descent
+    on the GPU, one CUDA-graph replay; ``poses`` is updated in place.  Returns
+    the final energies."""
+    _check_poses(poses, deck)
+    n = poses.shape[1]
+    if energies is None:
+        energies = torch.empty(n, dtype=torch.float32, device=poses.device)
+    o = _opts(opts, **kw)
+    rc = load().bude_refine(deck.handle, ctypes.c_void_p(poses.data_ptr()), n, int(steps),
+                            float(step0), ctypes.c_void_p(energies.data_ptr()), ctypes.byref(o),
+                            _stream_ptr(stream))
+    _check(rc)
+    return energies
 
 
 class PoseEnergy(torch.autograd.Function):

@@ -436,6 +436,8 @@ void drop_batches_using(const bude_deck* d)
 
 }  // namespace
 
+static void drop_refines_using(const bude_deck* d);
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -551,6 +553,7 @@ int bude_destroy_deck(bude_deck* d)
 {
     if (!d) return BUDE_OK;
     drop_batches_using(d);
+    drop_refines_using(d);
     cudaDeviceSynchronize();
     cudaFree(d->pro);
     cudaFree(d->lig);
@@ -764,4 +767,161 @@ extern "C" BUDE_API int bude_energies_noalloc(bude_deck* deck, const float* pose
     CK(cudaMemsetAsync(sc->counter, 0, (size_t)pl.n_tiles * sizeof(unsigned), s),
        "ticket clear");
     return launch_plan(pl, r, nullptr, sc->partial, sc->counter, s);
+}
+
+// ---------------------------------------------------------------------------
+// On-device pose refinement: steps of adjoint + propose + accept, captured
+// once into a CUDA graph per argument set and replayed.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr float kRefineGrow = 1.25f;
+constexpr float kRefineShrink = 0.5f;
+
+struct RefineKey {
+    int dev;
+    Resolved r;
+    const void* deck;
+    const void* poses;
+    const void* energies;
+    long long n;
+    int steps;
+    float step0;
+    bool operator<(const RefineKey& o) const { return memcmp(this, &o, sizeof *this) < 0; }
+};
+
+struct RefinePlan {
+    float* buf = nullptr;  // E[n] g[6n] trial[6n] Et[n] gt[6n] alpha[n]
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const bude_deck* deck = nullptr;
+    int launches = 0;
+    ~RefinePlan()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (buf) cudaFree(buf);
+    }
+};
+
+std::mutex g_refine_mutex;
+std::map<RefineKey, RefinePlan*> g_refines;
+
+}  // namespace
+
+static void drop_refines_using(const bude_deck* d)
+{
+    std::lock_guard<std::mutex> lk(g_refine_mutex);
+    for (auto it = g_refines.begin(); it != g_refines.end();) {
+        if (it->second->deck == d) {
+            delete it->second;
+            it = g_refines.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+extern "C" BUDE_API int bude_refine(bude_deck* deck, float* poses, int64_t n, int32_t steps,
+                                    float step0, float* energies, const bude_options* opts,
+                                    void* stream)
+{
+    g_launches = 0;
+    if (!deck) return fail(BUDE_ERR_INVALID_ARG, "deck is NULL");
+    if (n < 0 || steps < 0) return fail(BUDE_ERR_INVALID_ARG, "negative n or steps");
+    if (!(step0 > 0.f) || !std::isfinite(step0))
+        return fail(BUDE_ERR_INVALID_ARG, "step0 must be positive and finite");
+    if (n == 0) return BUDE_OK;
+    if (!poses || !energies) return fail(BUDE_ERR_INVALID_ARG, "poses or energies is NULL");
+    Resolved r;
+    int rc = resolve_options(opts, true, &r);
+    if (rc) return rc;
+    int dev;
+    if ((rc = current_device(&dev))) return rc;
+    if (dev != deck->device)
+        return fail(BUDE_ERR_INVALID_ARG, "deck lives on device %d, current device is %d",
+                    deck->device, dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((long long)deck->n_lig * deck->n_pro == 0) {
+        CK(cudaMemsetAsync(energies, 0, (size_t)n * sizeof(float), s), "memset");
+        return BUDE_OK;
+    }
+    RefineKey key;
+    memset(&key, 0, sizeof key);
+    key.dev = dev;
+    key.r = r;
+    key.deck = deck;
+    key.poses = poses;
+    key.energies = energies;
+    key.n = n;
+    key.steps = steps;
+    key.step0 = step0;
+    RefinePlan* rp = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_refine_mutex);
+        auto it = g_refines.find(key);
+        if (it != g_refines.end()) rp = it->second;
+    }
+    if (!rp) {
+        rp = new RefinePlan;
+        rp->deck = deck;
+        auto bail = [&](int code) { delete rp; return code; };
+        const size_t N = (size_t)n;
+        cudaError_t e = cudaMalloc((void**)&rp->buf, 22 * N * sizeof(float));
+        if (e) return bail(cuda_fail(e, "refine buffers"));
+        float* E = rp->buf;
+        float* g = E + N;
+        float* trial = g + 6 * N;
+        float* Et = trial + 6 * N;
+        float* gt = Et + N;
+        float* alpha = gt + 6 * N;
+        Plan p0, p1;
+        rc = make_plan({deck}, {poses}, {(long long)n}, {E}, {g}, r, true, dev, &p0);
+        if (rc) return bail(rc);
+        rc = make_plan({deck}, {trial}, {(long long)n}, {Et}, {gt}, r, true, dev, &p1);
+        if (rc) return bail(rc);
+        rc = ensure_workspace(&deck->partial, &deck->partial_bytes, &deck->counter,
+                              &deck->counter_count, partial_bytes_for(p0, r, true),
+                              (size_t)p0.n_tiles, s);
+        if (rc) return bail(rc);
+        e = cudaStreamSynchronize(s);
+        if (e) return bail(cuda_fail(e, "refine synchronisation"));
+        cudaStream_t cs;
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e) return bail(cuda_fail(e, "capture stream"));
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e) { cudaStreamDestroy(cs); return bail(cuda_fail(e, "begin capture")); }
+        int64_t saved = g_launches;
+        int lrc = BUDE_OK;
+        cudaError_t ke = launch_refine_init(alpha, n, step0, cs);
+        ++g_launches;
+        if (ke == cudaSuccess) lrc = launch_plan(p0, r, nullptr, deck->partial, deck->counter, cs);
+        for (int it = 0; it < steps && ke == cudaSuccess && lrc == BUDE_OK; ++it) {
+            ke = launch_refine_propose(poses, g, alpha, trial, n, cs);
+            ++g_launches;
+            if (ke != cudaSuccess) break;
+            lrc = launch_plan(p1, r, nullptr, deck->partial, deck->counter, cs);
+            if (lrc != BUDE_OK) break;
+            ke = launch_refine_accept(poses, E, g, trial, Et, gt, alpha, n, kRefineGrow,
+                                      kRefineShrink, cs);
+            ++g_launches;
+        }
+        cudaError_t ce = cudaSuccess;
+        if (ke == cudaSuccess && lrc == BUDE_OK)
+            ce = cudaMemcpyAsync(energies, E, N * sizeof(float), cudaMemcpyDeviceToDevice, cs);
+        rp->launches = (int)(g_launches - saved);
+        e = cudaStreamEndCapture(cs, &rp->graph);
+        cudaStreamDestroy(cs);
+        if (lrc) return bail(lrc);
+        if (ke) return bail(cuda_fail(ke, "refine kernel launch"));
+        if (ce) return bail(cuda_fail(ce, "refine energy copy"));
+        if (e) return bail(cuda_fail(e, "end capture"));
+        e = cudaGraphInstantiate(&rp->exec, rp->graph, 0);
+        if (e) return bail(cuda_fail(e, "graph instantiation"));
+        std::lock_guard<std::mutex> lk(g_refine_mutex);
+        g_refines[key] = rp;
+    }
+    CK(cudaGraphLaunch(rp->exec, s), "graph launch");
+    g_launches = rp->launches;
+    return BUDE_OK;
 }

@@ -24,4 +24,11 @@ cudaError_t launch_build_tables(const float4* lig_src, int n_lig, const float4* 
                                 float4* lig_dst, PairF* tabF, PairG* tabG, PairD* tabD,
                                 int* row_type, int* n_rows, unsigned* err, cudaStream_t s);
 
+cudaError_t launch_refine_init(float* alpha, long long n, float step0, cudaStream_t s);
+cudaError_t launch_refine_propose(const float* p, const float* g, const float* alpha,
+                                  float* trial, long long n, cudaStream_t s);
+cudaError_t launch_refine_accept(float* p, float* E, float* g, const float* trial,
+                                 const float* Et, const float* gt, float* alpha, long long n,
+                                 float grow, float shrink, cudaStream_t s);
+
 }  // namespace bude

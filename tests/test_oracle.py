@@ -330,3 +330,39 @@ def test_gradient_of_rotation_about_z_is_torque_component():
                 g[i] = (Ep - Em) / (2 * h)
             tau += np.cross(xp[l] - t, g)
         assert G[2, k] == pytest.approx(tau[2], rel=1e-5, abs=1e-5)
+
+
+# --- refinement -------------------------------------------------------------
+
+def test_refine_single_pair_reaches_the_contact_minimum():
+    """Types A (donor) and B (acceptor): e = 20 (s/3)^2 [s<0] - 2 phi(s/4) has
+    its minimum e = -2 at s = 0, i.e. d = R = 3, E = -1.  Starting at d = 4.5
+    (E = -175/256) the refinement must approach d = 3 from above."""
+    ta, tb = GOLD_TYPES["A"], GOLD_TYPES["B"]
+    D = _single_pair_deck(ta, tb, 0.0)
+    D["pro_xyz"] = np.array([[0.0, 0.0, 0.0]])
+    P0 = np.zeros((6, 1))
+    P0[3, 0] = 4.5                      # ligand atom at (4.5, 0, 0)
+    P, E, alpha = oracle.refine(D, P0, steps=60, step0=0.2)
+    d = np.linalg.norm(P[3:, 0])
+    assert E[0] == pytest.approx(-1.0, abs=1e-3)
+    assert 2.95 < d < 3.05
+    # the energy never increases along the way
+    prev = oracle.energies(D, P0)[0]
+    for k in (1, 2, 5, 10, 30):
+        _, Ek, _ = oracle.refine(D, P0, steps=k, step0=0.2)
+        assert Ek[0] <= prev + 1e-15
+        prev = Ek[0]
+
+
+def test_refine_never_raises_energy_and_keeps_rejected_poses():
+    D = _as64(synth.make_deck(25, 8, 150, 6, 12))
+    E0 = oracle.energies(D, D["poses"])
+    P, E, alpha = oracle.refine(D, D["poses"], steps=6, step0=0.05)
+    assert np.all(E <= E0)
+    np.testing.assert_allclose(oracle.energies(D, P), E, rtol=1e-12, atol=1e-12)
+    # alpha is step0 times grow^a shrink^r with a + r = steps
+    ratios = np.log(alpha / 0.05)
+    for r in ratios:
+        ok = any(abs(r - (a * np.log(1.25) + (6 - a) * np.log(0.5))) < 1e-9 for a in range(7))
+        assert ok
