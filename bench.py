@@ -37,6 +37,29 @@ SM_MAX_MHZ = 2070.0
 FP32_LANES_PER_SM = 128
 
 
+# DRAM traffic of one full-size FAST launch, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, mean of 9 launches; see
+# profiles/pose_kernel_fast_full_64x2672x65536_launches.md).  Reported only
+# while the kernel source and the launch shape are the ones that were
+# measured.
+MEASURED_TRAFFIC = {"kernel_sha256_16": "3cbca1dd03edee38", "variant": "fast", "ppwi": 16,
+                    "block": 384, "bytes": 1870791.0}
+
+
+def measured_traffic(variant, ppwi, block, n_poses):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2509_21039_gb300", "csrc", "bude_kernels.cuh")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m = MEASURED_TRAFFIC
+    if (sha, variant, ppwi, block, n_poses) != (m["kernel_sha256_16"], m["variant"], m["ppwi"],
+                                                 m["block"], FULL["n_poses"]):
+        return None
+    return m["bytes"]
+
+
 def eq3_flops(n_lig, n_pro, n_poses, ppwi):
     """Eq. 3: per work-item 28 P + nlig (2 + 18 P + npro (10 + 30 P)), x poses / P."""
     per_item = 28 * ppwi + n_lig * (2 + 18 * ppwi + n_pro * (10 + 30 * ppwi))
@@ -74,6 +97,7 @@ class ClockSampler:
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.5)   # let nvidia-smi start before the warm-up steps
         except Exception:
             self.proc = None
         return self
@@ -363,7 +387,9 @@ def main():
     ppwi = resolved.ppwi
     roofline = {
         "bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
-        "frac": achieved / peak_max, "traffic": None,
+        "frac": achieved / peak_max,
+        "traffic": measured_traffic(args.variant, ppwi, resolved.block, n),
+        "algorithmic_bytes": int(n * 28 + 4 * (shape["n_pro"] + shape["n_lig"]) * 4),
         "kernel": f"pose_kernel<{args.variant}, P={ppwi}>",
         "flops_per_launch": alg,
         "flop_count": "Eq. 3 in the many-poses limit: 28 + nlig (18 + 30 npro) per pose",
