@@ -56,11 +56,14 @@ class Options(ctypes.Structure):
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libbude.so (raises if it has not been built)."""
+def load(path: str | None = None):
+    """Load libbude.so (raises if it has not been built).  The environment
+    variable BUDE_LIB selects another build of it, e.g. libbude_debug.so."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = os.environ.get("BUDE_LIB", LIB_PATH)
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build it with "
                            "`python -c 'import __graft_entry__ as g; g.build()'`")

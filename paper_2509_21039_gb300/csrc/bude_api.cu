@@ -320,6 +320,50 @@ int ensure_workspace(double** partial, size_t* pbytes, unsigned** counter, size_
     return BUDE_OK;
 }
 
+// Device error word of BUDE_DEVICE_CHECKS builds: one per device, looked up
+// once (its host-side symbol is only a stand-in for the device address).
+static __device__ unsigned g_device_err;
+
+unsigned* device_err_word()
+{
+#ifdef BUDE_DEVICE_CHECKS
+    static std::mutex m;
+    static std::map<int, unsigned*> ptrs;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(m);
+    auto it = ptrs.find(dev);
+    if (it != ptrs.end()) return it->second;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_device_err) != cudaSuccess) return nullptr;
+    ptrs[dev] = static_cast<unsigned*>(p);
+    return static_cast<unsigned*>(p);
+#else
+    return nullptr;
+#endif
+}
+
+// BUDE_DEVICE_CHECKS builds: wait for the call's kernels, read and clear the
+// device error word.  Release builds: nothing.
+int device_checks(cudaStream_t s)
+{
+#ifdef BUDE_DEVICE_CHECKS
+    unsigned* w = device_err_word();
+    if (!w) return fail(BUDE_ERR_CUDA, "device error word unavailable");
+    unsigned h = 0;
+    CK(cudaMemcpyAsync(&h, w, sizeof h, cudaMemcpyDeviceToHost, s), "error word read");
+    CK(cudaStreamSynchronize(s), "error word sync");
+    if (h) {
+        CK(cudaMemsetAsync(w, 0, sizeof h, s), "error word clear");
+        CK(cudaStreamSynchronize(s), "error word sync");
+        return fail(BUDE_ERR_DEVICE_FLAG, "device check failed: bits %#x", h);
+    }
+#else
+    (void)s;
+#endif
+    return BUDE_OK;
+}
+
 int launch_plan(const Plan& pl, const Resolved& r, const Instance* dev_table, double* partial,
                 unsigned* counter, cudaStream_t s)
 {
@@ -331,6 +375,10 @@ int launch_plan(const Plan& pl, const Resolved& r, const Instance* dev_table, do
     a.n_total = pl.n_total;
     a.partial = partial;
     a.counter = counter;
+    a.err = device_err_word();
+    a.n_slots = (long long)pl.grid + pl.n_tiles;
+    a.n_tiles = pl.n_tiles;
+    a.smem_bytes = pl.smem;
     void* params[] = {&a};
     CK(cudaLaunchKernel(pl.fn, dim3(pl.grid), dim3(r.block), params, pl.smem, s), "kernel launch");
     ++g_launches;
@@ -376,7 +424,9 @@ int run_single(bude_deck* deck, const float* poses, int64_t n, float* energies, 
                           &deck->counter_count, partial_bytes_for(pl, r, G), (size_t)pl.n_tiles,
                           s);
     if (rc) return rc;
-    return launch_plan(pl, r, nullptr, deck->partial, deck->counter, s);
+    rc = launch_plan(pl, r, nullptr, deck->partial, deck->counter, s);
+    if (rc) return rc;
+    return device_checks(s);
 }
 
 // ---- batched plans -------------------------------------------------------
@@ -656,6 +706,7 @@ int bude_energies_batched(bude_deck* const* decks, const float* const* poses, co
         cudaStream_t cs;
         cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
         if (e) return bail(cuda_fail(e, "capture stream"));
+        device_err_word();  // resolve the check word's address before capturing
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e) { cudaStreamDestroy(cs); return bail(cuda_fail(e, "begin capture")); }
         int launches = 0;
@@ -683,7 +734,7 @@ int bude_energies_batched(bude_deck* const* decks, const float* const* poses, co
     }
     CK(cudaGraphLaunch(bp->exec, s), "graph launch");
     g_launches = bp->launches;
-    return BUDE_OK;
+    return device_checks(s);
 }
 
 }  // extern "C"
@@ -766,7 +817,9 @@ extern "C" BUDE_API int bude_energies_noalloc(bude_deck* deck, const float* pose
     // tickets must start at zero; the partial sums are written before read
     CK(cudaMemsetAsync(sc->counter, 0, (size_t)pl.n_tiles * sizeof(unsigned), s),
        "ticket clear");
-    return launch_plan(pl, r, nullptr, sc->partial, sc->counter, s);
+    rc = launch_plan(pl, r, nullptr, sc->partial, sc->counter, s);
+    if (rc) return rc;
+    return device_checks(s);
 }
 
 // ---------------------------------------------------------------------------
@@ -889,6 +942,7 @@ extern "C" BUDE_API int bude_refine(bude_deck* deck, float* poses, int64_t n, in
         cudaStream_t cs;
         e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
         if (e) return bail(cuda_fail(e, "capture stream"));
+        device_err_word();  // resolve the check word's address before capturing
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e) { cudaStreamDestroy(cs); return bail(cuda_fail(e, "begin capture")); }
         int64_t saved = g_launches;
@@ -923,5 +977,5 @@ extern "C" BUDE_API int bude_refine(bude_deck* deck, float* poses, int64_t n, in
     }
     CK(cudaGraphLaunch(rp->exec, s), "graph launch");
     g_launches = rp->launches;
-    return BUDE_OK;
+    return device_checks(s);
 }
