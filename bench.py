@@ -157,6 +157,18 @@ def cpu_baseline_leg(deck, n_poses_total, budget_s=12.0, threads=-1):
     return n / dt, n, dt, cores, E, A
 
 
+def cpu_single_thread(deck, budget_s=3.0):
+    """The oracle on one host core: poses/s on a sample of ~budget_s."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.energies(deck, deck["poses"][:, :2], n_threads=0)
+    dt = time.perf_counter() - t0
+    k = max(2, int(2 * budget_s / max(dt, 1e-3)))
+    t0 = time.perf_counter()
+    oracle.energies(deck, deck["poses"][:, :k], n_threads=0)
+    return k / (time.perf_counter() - t0), k
+
+
 def batched_vs_plain(bude, synth, tune, dev, timed, variant="fast", count=64, seed=3):
     """64 uneven decks: one persistent graph-replayed launch vs 64 plain launches."""
     import torch
@@ -242,6 +254,23 @@ def refine_throughput(bude, synth, tune, dev, timed, variant="fast", steps=10):
             "variant": variant, "ms": t, "pose_steps_per_s": steps * P.shape[1] / (t / 1e3),
             "graph_launches_per_call": 1, "kernels_per_call": launches // 5,
             "mean_energy_before": e0, "mean_energy_after": E.mean().item()}
+
+
+def param_grad_throughput(bude, synth, dev, timed, variant="fast"):
+    """Gradient of the pose-energy sum w.r.t. ligand coordinates and forcefield
+    parameters over 16384 poses of the 64 x 2672 deck."""
+    import torch
+    D = synth.make_deck(4, **synth.GRAD)
+    deck = bude.Deck(D, device=dev)
+    P = torch.from_numpy(D["poses"]).to(dev)
+    o = bude.LaunchOptions(variant=variant, ppwi=4, block=256)
+    ms, launches = timed(lambda: bude.param_grad(deck, P, opts=o), 5, 2)
+    deck.close()
+    t = statistics.mean(ms)
+    return {"workload": "dL/d(ligand xyz, radius, hardness, elsc), L = sum of 16384 pose "
+                        "energies, 64 lig x 2672 pro, seed 4",
+            "variant": variant, "ms": t, "poses_per_s": P.shape[1] / (t / 1e3),
+            "kernels_per_call": launches // 5}
 
 
 def reference_arm(args):
@@ -395,6 +424,9 @@ def main():
         "flop_count": "Eq. 3 in the many-poses limit: 28 + nlig (18 + 30 npro) per pose",
         "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz",
         "eq3_tflops_at_ppwi": eq3_flops(shape["n_lig"], shape["n_pro"], n, ppwi) / (ms_mean / 1e3) / 1e12,
+        # FLOPs the FP32 kernel executes per pose-pair: FADD 3, FMUL 1 + FFMA 2
+        # (distance), steric 5, two switches 7 each (FFMA = 2) = 27, plus a root
+        "executed_tflops": 27.0 * shape["n_lig"] * shape["n_pro"] * n / (ms_mean / 1e3) / 1e12,
     }
     if clocks:
         clk_peak = sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12
@@ -403,6 +435,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "poses/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mean,
+        "ms_per_step_median": statistics.median(ms), "ms_per_step_best": min(ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": (f"deck {shape['n_lig']} lig x {shape['n_pro']} pro x "
@@ -423,13 +456,17 @@ def main():
         line["batched"] = batched_vs_plain(bude, synth, tune, dev, timed)
         line["adjoint"] = adjoint_throughput(bude, synth, tune, dev, timed)
         line["refine"] = refine_throughput(bude, synth, tune, dev, timed)
+        line["param_grad"] = param_grad_throughput(bude, synth, dev, timed)
 
     # CPU-baseline leg: the FP64 oracle on a bounded sample of the same poses.
     # Its sample energies also give each variant's error on that sample.
     if not args.no_cpu_baseline:
         v, k, dt, cores, ref, A = cpu_baseline_leg(D, n)
+        v1, k1 = cpu_single_thread(D)
         line["cpu_baseline"] = {"value": v, "unit": "poses/s", "cores": cores, "kind": "oracle",
-                                "sample": f"first {k} poses of the same deck, FP64, {dt:.1f} s"}
+                                "sample": f"first {k} poses of the same deck, FP64, {dt:.1f} s",
+                                "single_thread_value": v1,
+                                "single_thread_sample": f"first {k1} poses, 1 thread"}
         if not args.no_extras:
             variants = {}
             # FP64 runs ~60x slower on GB300: time it on the first 4096 poses
@@ -456,6 +493,7 @@ def main():
                                    "abs_err_median": float(np.median(ab)),
                                    "abs_err_max": float(ab.max()),
                                    "rel_err_median": float(np.median(rel)),
+                                   "rel_err_p99": float(np.percentile(rel, 99)),
                                    "rel_err_max": float(rel.max()),
                                    "error_sample_poses": int(len(rf)),
                                    "timed_poses": int(npos)}

@@ -225,6 +225,28 @@ BUDE_API int bude_selfcheck_sqrt(uint64_t* mismatches, uint32_t* first_bad, void
 BUDE_API int bude_refine(bude_deck* deck, float* poses, int64_t n, int32_t steps, float step0,
                          float* energies, const bude_options* opts, void* stream);
 
+/*
+ * bude_param_grad -- gradient of a weighted sum of pose energies,
+ * L = sum_k w_k E_k, with respect to the ligand atom coordinates (in the
+ * ligand's own frame, before the pose) and the per-type forcefield
+ * parameters radius, hardness and elsc: the quantities forcefield fitting and
+ * ligand design take from a scoring function.  (The paper benchmarks the
+ * energy only; this differentiates it with respect to its other inputs.)
+ *
+ * weights:  device float32 [n], or NULL for all ones.
+ * lig_grad: device float32 [n_lig][3], dL/d(x, y, z) per ligand atom.
+ * ff_grad:  device float32 [n_types][3], dL/d(radius, hardness, elsc).
+ * The hbtype class is discrete and has no gradient.  Variants BUDE_FP32_IEEE
+ * and BUDE_FP32_FAST (COMP runs as IEEE); FP64 returns BUDE_ERR_UNSUPPORTED.
+ * Sums are accumulated in FP64 in shared memory and added over CTAs in a
+ * fixed order; shared-memory atomics make the last FP64 bits depend on
+ * scheduling, which the float32 outputs do not see.  Uses the deck's
+ * workspace: calls on one deck must not overlap.
+ */
+BUDE_API int bude_param_grad(bude_deck* deck, const float* poses, int64_t n,
+                             const float* weights, float* lig_grad, float* ff_grad,
+                             const bude_options* opts, void* stream);
+
 /* Default options the library uses for a variant when a field is zero. */
 BUDE_API int bude_get_default_options(int32_t variant, bude_options* out);
 BUDE_API int bude_set_default_options(const bude_options* opts);

@@ -64,6 +64,8 @@ def _load():
         lib.oracle_energies.argtypes = deck_args + [i64, dp, dp, dp, ci]
         lib.oracle_pose_grad.restype = ci
         lib.oracle_pose_grad.argtypes = deck_args + [i64, dp, dp, dp, dp, ci]
+        lib.oracle_param_grad.restype = ci
+        lib.oracle_param_grad.argtypes = deck_args + [i64, dp, dp, dp, dp]
         lib.oracle_max_threads.restype = ci
         lib.oracle_max_threads.argtypes = []
         _lib = lib
@@ -162,6 +164,24 @@ def pose_grad(deck, poses, n_threads: int = 0, with_scale: bool = False):
     if rc != 0:
         raise ValueError("oracle_pose_grad rejected the deck")
     return (E, G, S) if with_scale else (E, G)
+
+
+def param_grad(deck, poses, weights=None):
+    """Gradient of L = sum_k w_k E_k (float64): (dL/d ligand xyz [n_lig][3],
+    dL/d (radius, hardness, elsc) [n_types][3])."""
+    lib = _load()
+    args, keep = _deck_args(deck)
+    P = np.ascontiguousarray(poses, np.float64).reshape(6, -1)
+    n = P.shape[1]
+    w = None if weights is None else np.ascontiguousarray(weights, np.float64)
+    GL = np.zeros((len(deck["lig_type"]), 3), np.float64)
+    GF = np.zeros((len(deck["radius"]), 3), np.float64)
+    rc = lib.oracle_param_grad(*args, n, _dptr(P), _dptr(w) if w is not None else None,
+                               _dptr(GL), _dptr(GF))
+    del keep
+    if rc != 0:
+        raise ValueError("oracle_param_grad rejected the deck")
+    return GL, GF
 
 
 # --- pose refinement (the docking step after scoring) ----------------------

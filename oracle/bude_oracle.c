@@ -374,3 +374,85 @@ int oracle_max_threads(void)
     return 1;
 #endif
 }
+
+
+/*
+ * Gradient of L = sum_k w_k energy[k] with respect to the ligand atom
+ * coordinates (in the ligand frame, before the pose) and to the per-type
+ * forcefield parameters radius, hardness and elsc.
+ *
+ *   dL/dx_l  = sum_k w_k 0.5 sum_p R_k^T e'(d) (x'_l - x_p) / d
+ * and, for a pair of types a (ligand) and b (protein), from the
+ * combination rules R = r_a + r_b, H = (h_a + h_b)/2, Q = q_a q_b:
+ *   de/dr_a = de/dr_b = de/dR
+ *   de/dh_a = de/dh_b = (1/2) de/dH
+ *   de/dq_a = K_E w q_b phi(s/D_E),  de/dq_b = K_E w q_a phi(s/D_E)
+ * with de/dR = -2 H (s/R) d / R^2 [s<0] - QW phi'(s/D_E)/D_E
+ *              - S phi'(s/D_D)/D_D  and  de/dH = (s/R)^2 [s<0].
+ * lig_grad is [n_lig][3], ff_grad is [n_types][3] (radius, hardness, elsc);
+ * weights may be NULL (all ones).  A pair at d = 0 adds nothing to lig_grad.
+ */
+int oracle_param_grad(int n_lig, const double* lig_xyz, const int32_t* lig_type,
+                      int n_pro, const double* pro_xyz, const int32_t* pro_type,
+                      int n_types, const double* radius, const double* hardness,
+                      const double* elsc, const int32_t* hbtype,
+                      int64_t n_poses, const double* poses, const double* weights,
+                      double* lig_grad, double* ff_grad)
+{
+    oracle_deck D = {n_lig, n_pro, n_types, lig_xyz, lig_type, pro_xyz,
+                     pro_type, radius, hardness, elsc, hbtype};
+    if (n_poses < 0 || check_deck(&D) != 0) return -1;
+    for (int i = 0; i < 3 * n_lig; ++i) lig_grad[i] = 0.0;
+    for (int i = 0; i < 3 * n_types; ++i) ff_grad[i] = 0.0;
+    for (int64_t k = 0; k < n_poses; ++k) {
+        double wk = weights ? weights[k] : 1.0;
+        double R[9];
+        oracle_rotation(poses[0 * n_poses + k], poses[1 * n_poses + k],
+                        poses[2 * n_poses + k], R);
+        double t[3] = {poses[3 * n_poses + k], poses[4 * n_poses + k],
+                       poses[5 * n_poses + k]};
+        for (int l = 0; l < n_lig; ++l) {
+            const double* x = lig_xyz + 3 * l;
+            double xp[3];
+            for (int i = 0; i < 3; ++i)
+                xp[i] = R[3 * i + 0] * x[0] + R[3 * i + 1] * x[1] +
+                        R[3 * i + 2] * x[2] + t[i];
+            int a = lig_type[l];
+            double g[3] = {0, 0, 0};
+            for (int p = 0; p < n_pro; ++p) {
+                int b = pro_type[p];
+                const double* y = pro_xyz + 3 * p;
+                double dv[3] = {xp[0] - y[0], xp[1] - y[1], xp[2] - y[2]};
+                double d = sqrt(dot3(dv, dv));
+                pair_params pp = deck_pair(&D, a, b);
+                double s = d - pp.R;
+                double dR = -pp.QW * switch_dphi(s / ORACLE_DE) / ORACLE_DE -
+                            pp.S * switch_dphi(s / ORACLE_DD) / ORACLE_DD;
+                double dH = 0.0;
+                if (s < 0.0) {
+                    dR += -2.0 * pp.H * (s / pp.R) * d / (pp.R * pp.R);
+                    dH = (s / pp.R) * (s / pp.R);
+                }
+                double wab = ((hbtype[a] == 1 && hbtype[b] == 2) ||
+                              (hbtype[a] == 2 && hbtype[b] == 1)) ? 2.0 : 1.0;
+                double phiE = switch_phi(s / ORACLE_DE);
+                double f = 0.5 * wk;
+                ff_grad[3 * a + 0] += f * dR;
+                ff_grad[3 * b + 0] += f * dR;
+                ff_grad[3 * a + 1] += f * 0.5 * dH;
+                ff_grad[3 * b + 1] += f * 0.5 * dH;
+                ff_grad[3 * a + 2] += f * ORACLE_KE * wab * elsc[b] * phiE;
+                ff_grad[3 * b + 2] += f * ORACLE_KE * wab * elsc[a] * phiE;
+                if (d > 0.0) {
+                    double c = pair_denergy_pp(&pp, d) / d;
+                    for (int i = 0; i < 3; ++i) g[i] += c * dv[i];
+                }
+            }
+            /* dL/dx_l += w_k 0.5 R^T g */
+            for (int j = 0; j < 3; ++j)
+                lig_grad[3 * l + j] += 0.5 * wk *
+                    (R[0 * 3 + j] * g[0] + R[1 * 3 + j] * g[1] + R[2 * 3 + j] * g[2]);
+        }
+    }
+    return 0;
+}

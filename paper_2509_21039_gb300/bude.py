@@ -82,6 +82,7 @@ def load(path: str | None = None):
                                        ctypes.POINTER(Options), vp]),
         "bude_pose_grad": (ci, [vp, vp, i64, vp, vp, ctypes.POINTER(Options), vp]),
         "bude_refine": (ci, [vp, vp, i64, i32, ctypes.c_float, vp, ctypes.POINTER(Options), vp]),
+        "bude_param_grad": (ci, [vp, vp, i64, vp, vp, vp, ctypes.POINTER(Options), vp]),
         "bude_get_default_options": (ci, [i32, ctypes.POINTER(Options)]),
         "bude_set_default_options": (ci, [ctypes.POINTER(Options)]),
         "bude_last_launch_count": (i64, []),
@@ -321,6 +322,28 @@ def refine_device(deck: Deck, poses: torch.Tensor, steps: int = 10, step0: float
                             _stream_ptr(stream))
     _check(rc)
     return energies
+
+
+def param_grad(deck: Deck, poses: torch.Tensor, weights: torch.Tensor | None = None,
+               opts=None, stream=None, **kw):
+    """bude_param_grad: (dL/d ligand xyz [n_lig, 3], dL/d (radius, hardness,
+    elsc) [n_types, 3]) for L = sum_k w_k E_k."""
+    _check_poses(poses, deck)
+    n = poses.shape[1]
+    if weights is not None:
+        if weights.shape != (n,) or weights.dtype != torch.float32 or weights.device != poses.device:
+            raise ValueError("weights must be a float32 [n] tensor on the poses' device")
+        weights = weights.contiguous()
+    gl = torch.empty((deck.n_lig, 3), dtype=torch.float32, device=poses.device)
+    gf = torch.empty((deck.n_types, 3), dtype=torch.float32, device=poses.device)
+    o = _opts(opts, **kw)
+    rc = load().bude_param_grad(deck.handle, ctypes.c_void_p(poses.data_ptr()), n,
+                                ctypes.c_void_p(weights.data_ptr()) if weights is not None else None,
+                                ctypes.c_void_p(gl.data_ptr()) if deck.n_lig else None,
+                                ctypes.c_void_p(gf.data_ptr()), ctypes.byref(o),
+                                _stream_ptr(stream))
+    _check(rc)
+    return gl, gf
 
 
 class PoseEnergy(torch.autograd.Function):

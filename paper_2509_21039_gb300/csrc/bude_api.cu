@@ -28,6 +28,7 @@ struct bude_deck {
     PairG* tabG = nullptr;
     PairD* tabD = nullptr;
     int* row_type = nullptr; // [n_rows]
+    float4* ff = nullptr;    // [n_types] forcefield rows as given
     // scratch workspace of the plain and adjoint calls
     double* partial = nullptr;
     size_t partial_bytes = 0;
@@ -570,6 +571,9 @@ int bude_create_deck(const bude_deck_desc* desc, void* stream, bude_deck** out)
     CKD(cudaMalloc((void**)&d->tabG, pairs * sizeof(PairG)), "deck allocation");
     CKD(cudaMalloc((void**)&d->tabD, pairs * sizeof(PairD)), "deck allocation");
     CKD(cudaMalloc((void**)&d->row_type, (size_t)d->n_types * sizeof(int)), "deck allocation");
+    CKD(cudaMalloc((void**)&d->ff, (size_t)d->n_types * sizeof(float4)), "deck allocation");
+    CKD(cudaMemcpyAsync(d->ff, desc->ff, (size_t)d->n_types * sizeof(float4),
+                        cudaMemcpyDeviceToDevice, s), "forcefield copy");
     CKD(cudaMalloc((void**)&tmp, sizeof(Tmp)), "deck allocation");
     CKD(cudaMemsetAsync(tmp, 0, sizeof(Tmp), s), "memset");
     CKD(launch_pack_protein((const float4*)desc->pro_xyzt, d->pro, d->n_pro, d->n_types,
@@ -611,6 +615,7 @@ int bude_destroy_deck(bude_deck* d)
     cudaFree(d->tabG);
     cudaFree(d->tabD);
     cudaFree(d->row_type);
+    cudaFree(d->ff);
     cudaFree(d->partial);
     cudaFree(d->counter);
     delete d;
@@ -977,5 +982,86 @@ extern "C" BUDE_API int bude_refine(bude_deck* deck, float* poses, int64_t n, in
     }
     CK(cudaGraphLaunch(rp->exec, s), "graph launch");
     g_launches = rp->launches;
+    return device_checks(s);
+}
+
+// ---------------------------------------------------------------------------
+// Gradient of sum_k w_k E_k with respect to ligand coordinates and forcefield
+// ---------------------------------------------------------------------------
+extern "C" BUDE_API int bude_param_grad(bude_deck* deck, const float* poses, int64_t n,
+                                        const float* weights, float* lig_grad, float* ff_grad,
+                                        const bude_options* opts, void* stream)
+{
+    g_launches = 0;
+    if (!deck) return fail(BUDE_ERR_INVALID_ARG, "deck is NULL");
+    if (n < 0) return fail(BUDE_ERR_INVALID_ARG, "n = %lld < 0", (long long)n);
+    if (!lig_grad && deck->n_lig > 0) return fail(BUDE_ERR_INVALID_ARG, "lig_grad is NULL");
+    if (!ff_grad) return fail(BUDE_ERR_INVALID_ARG, "ff_grad is NULL");
+    if (n > 0 && !poses) return fail(BUDE_ERR_INVALID_ARG, "poses is NULL");
+    Resolved r;
+    int rc = resolve_options(opts, true, &r);
+    if (rc) return rc;
+    if (r.variant == BUDE_FP64)
+        return fail(BUDE_ERR_UNSUPPORTED, "bude_param_grad has FP32 variants only");
+    const int kv = r.variant == BUDE_FP32_FAST ? kFAST : kIEEE;
+    int dev;
+    if ((rc = current_device(&dev))) return rc;
+    if (dev != deck->device)
+        return fail(BUDE_ERR_INVALID_ARG, "deck lives on device %d, current device is %d",
+                    deck->device, dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long K = (long long)deck->n_lig * deck->n_pro;
+    if (n == 0 || K == 0) {
+        if (deck->n_lig) CK(cudaMemsetAsync(lig_grad, 0, (size_t)deck->n_lig * 3 * sizeof(float), s), "memset");
+        CK(cudaMemsetAsync(ff_grad, 0, (size_t)deck->n_types * 3 * sizeof(float), s), "memset");
+        return BUDE_OK;
+    }
+    const void* fn = kernel_param(kv, r.P);
+    if (!fn) return fail(BUDE_ERR_UNSUPPORTED, "poses per thread %d not built for bude_param_grad", r.P);
+    const DeviceInfo di = device_info(dev);
+    const size_t budget = smem_budget(di, r.cps);
+    const size_t fixed = param_smem_bytes(r.P, deck->n_lig, deck->n_rows, deck->n_types, 0);
+    if (fixed + 16 * 32 > budget)
+        return fail(BUDE_ERR_UNSUPPORTED, "gradient accumulators and pair table do not fit in shared memory");
+    int chunk = (int)std::min<size_t>((size_t)deck->n_pro, (budget - fixed) / 16);
+    if (r.tile > 0) chunk = std::min(chunk, r.tile);
+    const size_t smem = param_smem_bytes(r.P, deck->n_lig, deck->n_rows, deck->n_types, chunk);
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+       "cudaFuncSetAttribute");
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, r.block, smem), "occupancy query");
+    if (occ < 1) return fail(BUDE_ERR_UNSUPPORTED, "block %d cannot be resident", r.block);
+    const long long TP = 32ll * r.P;
+    const long long tiles = (n + TP - 1) / TP;
+    const long long N = tiles * K;
+    long long grid = (long long)di.sms * std::min(occ, r.cps);
+    if (grid > N) grid = N;
+    const int acc_len = deck->n_lig * 3 + deck->n_rows * deck->n_types * 3;
+    const size_t need = ((size_t)grid + 1) * (size_t)acc_len * sizeof(double);
+    rc = ensure_workspace(&deck->partial, &deck->partial_bytes, &deck->counter,
+                          &deck->counter_count, need, 0, s);
+    if (rc) return rc;
+    ParamArgs a;
+    memset(&a, 0, sizeof a);
+    a.pro = deck->pro;
+    a.lig = deck->lig;
+    a.pair = deck->tabG;
+    a.poses = poses;
+    a.weights = weights;
+    a.n_poses = n;
+    a.n_total = N;
+    a.cta_acc = deck->partial;
+    a.n_lig = deck->n_lig;
+    a.n_pro = deck->n_pro;
+    a.n_types = deck->n_types;
+    a.n_rows = deck->n_rows;
+    a.chunk = chunk;
+    void* params[] = {&a};
+    CK(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(r.block), params, smem, s), "kernel launch");
+    double* sums = deck->partial + (size_t)grid * acc_len;
+    CK(launch_param_reduce(deck->partial, (int)grid, deck->n_lig, deck->n_rows, deck->n_types,
+                           sums, deck->row_type, deck->ff, lig_grad, ff_grad, s),
+       "reduction launch");
+    g_launches = 3;
     return device_checks(s);
 }

@@ -115,13 +115,71 @@ __global__ void build_tables_kernel(const float4* __restrict__ lig_src, int n_li
     }
 }
 
+// Single CTA: stable sort of the protein atoms by type (a counting sort done
+// one present type at a time with block-wide ballots), so that atoms of one
+// type are consecutive.  The energy is a sum over atoms, so the order is
+// free; the forcefield-gradient kernel relies on the runs.  Atoms with an
+// invalid type are dropped here and reported by pack_protein_kernel.
+__global__ void sort_protein_kernel(const float4* __restrict__ src, float4* __restrict__ dst,
+                                    int n, int n_types)
+{
+    __shared__ int s_count[BUDE_MAX_TYPES];
+    __shared__ int s_warp[32];
+    __shared__ int s_base, s_total;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    for (int t = tid; t < n_types; t += blockDim.x) s_count[t] = 0;
+    if (tid == 0) s_base = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) {
+        const int t = __float_as_int(src[i].w);
+        if (t >= 0 && t < n_types) atomicAdd(&s_count[t], 1);
+    }
+    __syncthreads();
+    for (int t = 0; t < n_types; ++t) {
+        if (s_count[t] == 0) continue;  // uniform: every thread reads the same count
+        for (int base = 0; base < n; base += blockDim.x) {
+            const int i = base + tid;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+            bool f = false;
+            if (i < n) {
+                a = src[i];
+                f = __float_as_int(a.w) == t;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, f);
+            const int before = __popc(m & ((1u << lane) - 1u));
+            if (lane == 0) s_warp[warp] = __popc(m);
+            __syncthreads();
+            if (warp == 0) {
+                int v = lane < nwarps ? s_warp[lane] : 0;
+                int incl = v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += u;
+                }
+                if (lane < nwarps) s_warp[lane] = incl - v;  // exclusive prefix
+                if (lane == 31) s_total = incl;              // block total (nwarps <= 32)
+            }
+            __syncthreads();
+            if (f) dst[s_base + s_warp[warp] + before] = a;
+            __syncthreads();
+            if (tid == 0) s_base += s_total;
+            __syncthreads();
+        }
+    }
+}
+
 cudaError_t launch_pack_protein(const float4* src, float4* dst, int n, int n_types,
                                 unsigned* err, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     int blocks = (n + 255) / 256;
     if (blocks > 1024) blocks = 1024;
+    // validation pass (its copy is overwritten by the sorted one)
     pack_protein_kernel<<<blocks, 256, 0, s>>>(src, dst, n, n_types, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sort_protein_kernel<<<1, 1024, 0, s>>>(src, dst, n, n_types);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,24 @@ cudaError_t launch_build_tables(const float4* lig_src, int n_lig, const float4* 
                                 float4* lig_dst, PairF* tabF, PairG* tabG, PairD* tabD,
                                 int* row_type, int* n_rows, unsigned* err, cudaStream_t s);
 
+// Forcefield/ligand gradient kernel (bude_param.cu).
+struct ParamArgs {
+    const float4* pro;     // sorted by type
+    const float4* lig;     // row-mapped
+    const PairG* pair;     // [n_rows][n_types]
+    const float* poses;    // [6][n_poses]
+    const float* weights;  // [n_poses] or null (all ones)
+    long long n_poses;
+    long long n_total;     // tiles * n_lig * n_pro
+    double* cta_acc;       // [grid][n_lig*3 + n_rows*n_types*3]
+    int n_lig, n_pro, n_types, n_rows, chunk;
+};
+const void* kernel_param(int variant, int P);
+size_t param_smem_bytes(int P, int n_lig, int n_rows, int n_types, int chunk);
+cudaError_t launch_param_reduce(const double* cta_acc, int n_cta, int n_lig, int n_rows,
+                                int n_types, double* sums, const int* row_type, const float4* ff,
+                                float* lig_grad, float* ff_grad, cudaStream_t s);
+
 cudaError_t launch_refine_init(float* alpha, long long n, float step0, cudaStream_t s);
 cudaError_t launch_refine_propose(const float* p, const float* g, const float* alpha,
                                   float* trial, long long n, cudaStream_t s);

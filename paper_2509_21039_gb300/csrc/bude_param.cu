@@ -1,0 +1,321 @@
+// Gradient of a weighted sum of pose energies, L = sum_k w_k E_k, with
+// respect to the ligand atom coordinates and the per-type forcefield
+// parameters (radius, hardness, elsc): what forcefield fitting and ligand
+// design need from the scoring function.
+//
+// Same flat work space and shared-memory staging as the pose kernel, but
+// every CTA only accumulates: there are no per-pose outputs, so no cross-CTA
+// tile finish.  Per pair and pose the kernel needs, besides de/dd:
+//   de/dR = -de/dd + hs w^2   (hs = -2H/R; the steric part of de/dd is hs w)
+//   de/dH = w^2,   dphi_E = v_E^2 (3 - 2 v_E)
+// summed with weight w_k/2 over the lane's poses for the current run of
+// protein atoms of one type (the deck stores the protein sorted by type), and
+// added per run into shared FP64 accumulators for the (ligand row, protein
+// type) pair.  The ligand gradient R^T g is summed per ligand atom.  A second
+// pass adds the CTAs' accumulators in CTA order and applies the combination
+// rules (R = r_a + r_b, H = (h_a + h_b)/2, C_E = K_E q_a q_b w_ab).
+#include "bude_internal.h"
+
+namespace bude {
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int V, int P>
+__global__ void param_kernel(const ParamArgs a)
+{
+    constexpr int TP = 32 * P;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int W = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int acc_lig = a.n_lig * 3;
+    const int acc_len = acc_lig + a.n_rows * a.n_types * 3;
+    double* s_acc = reinterpret_cast<double*>(smem);                        // [acc_len]
+    size_t off = ((size_t)acc_len * sizeof(double) + 15) & ~size_t(15);
+    float* s_tr = reinterpret_cast<float*>(smem + off);                     // [12][TP]
+    float* s_w = s_tr + 12 * TP;                                            // [TP] w_k / 2
+    off += (size_t)13 * TP * sizeof(float);
+    PairG* s_pair = reinterpret_cast<PairG*>(smem + off);                   // [n_rows][n_types]
+    off += (size_t)a.n_rows * a.n_types * sizeof(PairG);
+    float4* s_pro = reinterpret_cast<float4*>(smem + off);                  // [chunk]
+
+    const long long N = a.n_total;
+    const long long C = gridDim.x;
+    const long long c = blockIdx.x;
+    long long x = c * N / C;
+    const long long xe = (c + 1) * N / C;
+
+    for (int i = threadIdx.x; i < acc_len; i += blockDim.x) s_acc[i] = 0.0;
+    for (int i = threadIdx.x; i < a.n_rows * a.n_types; i += blockDim.x) s_pair[i] = a.pair[i];
+    int staged_chunk = -1;
+    const long long K = (long long)a.n_lig * a.n_pro;
+
+    while (x < xe) {
+        const long long t = x / K;
+        const long long tile_k0 = t * K;
+        const long long seg_end = xe < tile_k0 + K ? xe : tile_k0 + K;
+        const long long pose0 = t * TP;
+        __syncthreads();
+        for (int s = threadIdx.x; s < TP; s += blockDim.x) {
+            long long k = pose0 + s;
+            const bool tail = k >= a.n_poses;
+            if (tail) k = a.n_poses - 1;
+            const long long n = a.n_poses;
+            float sx, cx, sy, cy, sz, cz;
+            if (V == kFAST) {
+                __sincosf(a.poses[k], &sx, &cx);
+                __sincosf(a.poses[n + k], &sy, &cy);
+                __sincosf(a.poses[2 * n + k], &sz, &cz);
+            } else {
+                sincosf(a.poses[k], &sx, &cx);
+                sincosf(a.poses[n + k], &sy, &cy);
+                sincosf(a.poses[2 * n + k], &sz, &cz);
+            }
+            s_tr[0 * TP + s] = cy * cz;
+            s_tr[1 * TP + s] = sx * sy * cz - cx * sz;
+            s_tr[2 * TP + s] = cx * sy * cz + sx * sz;
+            s_tr[3 * TP + s] = cy * sz;
+            s_tr[4 * TP + s] = sx * sy * sz + cx * cz;
+            s_tr[5 * TP + s] = cx * sy * sz - sx * cz;
+            s_tr[6 * TP + s] = -sy;
+            s_tr[7 * TP + s] = sx * cy;
+            s_tr[8 * TP + s] = cx * cy;
+            s_tr[9 * TP + s] = a.poses[3 * n + k];
+            s_tr[10 * TP + s] = a.poses[4 * n + k];
+            s_tr[11 * TP + s] = a.poses[5 * n + k];
+            s_w[s] = tail ? 0.f : 0.5f * (a.weights ? a.weights[k] : 1.f);
+        }
+        __syncthreads();
+
+        long long r0 = x - tile_k0;
+        const long long r1 = seg_end - tile_k0;
+        while (r0 < r1) {
+            const int CL = a.chunk;
+            const long long rowsK = (long long)a.n_lig * CL;
+            const int q = (int)(r0 / rowsK);
+            const long long cb = (long long)q * rowsK;
+            const int len_q = min(CL, a.n_pro - q * CL);
+            const long long cend = cb + (long long)a.n_lig * len_q;
+            const long long sub_end = r1 < cend ? r1 : cend;
+            if (q != staged_chunk) {
+                __syncthreads();
+                const float4* gsrc = a.pro + (size_t)q * CL;
+                for (int i = threadIdx.x; i < len_q; i += blockDim.x) s_pro[i] = gsrc[i];
+                __syncthreads();
+                staged_chunk = q;
+            }
+            const long long len = sub_end - r0;
+            long long i0 = r0 - cb + len * warp / W;
+            const long long i1 = r0 - cb + len * (warp + 1) / W;
+            int l = (int)(i0 / len_q);
+            int p = (int)(i0 - (long long)l * len_q);
+            float wv[P];
+#pragma unroll
+            for (int k = 0; k < P; ++k) wv[k] = s_w[lane + 32 * k];
+            while (i0 < i1) {
+                const long long row_base = (long long)l * len_q;
+                const int pend = (int)((i1 - row_base) < len_q ? (i1 - row_base) : len_q);
+                const float4 la = a.lig[l];
+                const int row = __float_as_int(la.w);
+                const volatile float* tr = s_tr;
+                float xl[P], yl[P], zl[P], ngx[P], ngy[P], ngz[P];
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    const int s = lane + 32 * k;
+                    xl[k] = tr[0 * TP + s] * la.x + tr[1 * TP + s] * la.y + tr[2 * TP + s] * la.z + tr[9 * TP + s];
+                    yl[k] = tr[3 * TP + s] * la.x + tr[4 * TP + s] * la.y + tr[5 * TP + s] * la.z + tr[10 * TP + s];
+                    zl[k] = tr[6 * TP + s] * la.x + tr[7 * TP + s] * la.y + tr[8 * TP + s] * la.z + tr[11 * TP + s];
+                    ngx[k] = 0.f; ngy[k] = 0.f; ngz[k] = 0.f;
+                }
+                double* acc_row = s_acc + acc_lig + (size_t)row * a.n_types * 3;
+                const PairG* prow = s_pair + (size_t)row * a.n_types;
+                float aR = 0.f, aH = 0.f, aE = 0.f;
+                int cur = -1;
+                for (int pp = p; pp < pend; ++pp) {
+                    const float4 at = s_pro[pp];
+                    const int tp = __float_as_int(at.w);
+                    if (tp != cur) {  // warp-uniform: every lane reads the same atom
+                        if (cur >= 0) {
+                            const float sR = warp_sum(aR), sH = warp_sum(aH), sE = warp_sum(aE);
+                            if (lane == 0) {
+                                atomicAdd(acc_row + cur * 3 + 0, (double)sR);
+                                atomicAdd(acc_row + cur * 3 + 1, (double)sH);
+                                atomicAdd(acc_row + cur * 3 + 2, (double)sE);
+                            }
+                        }
+                        cur = tp;
+                        aR = 0.f; aH = 0.f; aE = 0.f;
+                    }
+                    const PairG cp = prow[tp];
+#pragma unroll
+                    for (int k = 0; k < P; ++k) {
+                        const float dx = at.x - xl[k], dy = at.y - yl[k], dz = at.z - zl[k];
+                        const float d2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, kMinD2)));
+                        const float y = rsqrt_approx(d2);
+                        const float d = (V == kFAST) ? d2 * y : sqrt_rn_fma(d2, y);
+                        const float w = clamp01(fmaf(d, -cp.inv_r, 1.f));
+                        const float ve = clamp01(fmaf(d, -(float)(1.0 / kDE), cp.ce));
+                        const float vd = clamp01(fmaf(d, -(float)(1.0 / kDD), cp.cd));
+                        float dedd = cp.hs * w;
+                        dedd = fmaf(ve, fmaf(cp.ae1, ve, cp.ae0), dedd);
+                        dedd = fmaf(vd, fmaf(cp.ad1, vd, cp.ad0), dedd);
+                        const float f = dedd * y;
+                        ngx[k] = fmaf(f, dx, ngx[k]);
+                        ngy[k] = fmaf(f, dy, ngy[k]);
+                        ngz[k] = fmaf(f, dz, ngz[k]);
+                        const float w2 = w * w;
+                        aR = fmaf(wv[k], fmaf(cp.hs, w2, -dedd), aR);
+                        aH = fmaf(wv[k], w2, aH);
+                        aE = fmaf(wv[k], ve * ve * fmaf(-2.f, ve, 3.f), aE);
+                    }
+                }
+                if (cur >= 0) {
+                    const float sR = warp_sum(aR), sH = warp_sum(aH), sE = warp_sum(aE);
+                    if (lane == 0) {
+                        atomicAdd(acc_row + cur * 3 + 0, (double)sR);
+                        atomicAdd(acc_row + cur * 3 + 1, (double)sH);
+                        atomicAdd(acc_row + cur * 3 + 2, (double)sE);
+                    }
+                }
+                // dL/dx_l += sum_k (w_k/2) R_k^T g_k with g_k = -ng_k
+                float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    const int s = lane + 32 * k;
+                    const float gx = -wv[k] * ngx[k], gy = -wv[k] * ngy[k], gz = -wv[k] * ngz[k];
+                    v0 += tr[0 * TP + s] * gx + tr[3 * TP + s] * gy + tr[6 * TP + s] * gz;
+                    v1 += tr[1 * TP + s] * gx + tr[4 * TP + s] * gy + tr[7 * TP + s] * gz;
+                    v2 += tr[2 * TP + s] * gx + tr[5 * TP + s] * gy + tr[8 * TP + s] * gz;
+                }
+                v0 = warp_sum(v0);
+                v1 = warp_sum(v1);
+                v2 = warp_sum(v2);
+                if (lane == 0) {
+                    atomicAdd(s_acc + 3 * l + 0, (double)v0);
+                    atomicAdd(s_acc + 3 * l + 1, (double)v1);
+                    atomicAdd(s_acc + 3 * l + 2, (double)v2);
+                }
+                i0 = row_base + pend;
+                ++l;
+                p = 0;
+            }
+            r0 = sub_end;
+        }
+        x = seg_end;
+    }
+    __syncthreads();
+    double* out = a.cta_acc + (size_t)c * acc_len;
+    for (int i = threadIdx.x; i < acc_len; i += blockDim.x) out[i] = s_acc[i];
+}
+
+// Adds the CTAs' accumulators in CTA order: sums[i] = sum_c cta_acc[c][i].
+__global__ void param_sum_kernel(const double* __restrict__ cta_acc, int n_cta, int acc_len,
+                                 double* __restrict__ sums)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < acc_len; i += gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int c = 0; c < n_cta; ++c) v += cta_acc[(size_t)c * acc_len + i];
+        sums[i] = v;
+    }
+}
+
+// Chain rule from the (row, protein type) sums to per-type gradients, one
+// thread per output, each summing its contributions in a fixed order.
+__global__ void param_finish_kernel(const double* __restrict__ sums, int n_lig, int n_rows,
+                                    int n_types, const int* __restrict__ row_type,
+                                    const float4* __restrict__ ff, float* __restrict__ lig_grad,
+                                    float* __restrict__ ff_grad)
+{
+    const int acc_lig = n_lig * 3;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < acc_lig + n_types;
+         i += gridDim.x * blockDim.x) {
+        if (i < acc_lig) {
+            lig_grad[i] = (float)sums[i];
+            continue;
+        }
+        const int t = i - acc_lig;
+        const float4 ft = ff[t];
+        const int ht = __float_as_int(ft.w);
+        double gr = 0.0, gh = 0.0, gq = 0.0;
+        for (int r = 0; r < n_rows; ++r) {
+            const int ta = row_type[r];
+            const float4 fa = ff[ta];
+            const int ha = __float_as_int(fa.w);
+            for (int b = 0; b < n_types; ++b) {
+                const bool as_a = (ta == t), as_b = (b == t);
+                if (!as_a && !as_b) continue;
+                const double* v = sums + acc_lig + ((size_t)r * n_types + b) * 3;
+                const float4 fb = ff[b];
+                const int hb = __float_as_int(fb.w);
+                const double wab = ((ha == 1 && hb == 2) || (ha == 2 && hb == 1)) ? 2.0 : 1.0;
+                if (as_a) {
+                    gr += v[0];
+                    gh += 0.5 * v[1];
+                    gq += kKE * wab * (double)fb.z * v[2];
+                }
+                if (as_b) {
+                    gr += v[0];
+                    gh += 0.5 * v[1];
+                    gq += kKE * wab * (double)fa.z * v[2];
+                }
+            }
+        }
+        (void)ht;
+        ff_grad[3 * t + 0] = (float)gr;
+        ff_grad[3 * t + 1] = (float)gh;
+        ff_grad[3 * t + 2] = (float)gq;
+    }
+}
+
+template __global__ void param_kernel<kIEEE, 1>(const ParamArgs);
+template __global__ void param_kernel<kIEEE, 2>(const ParamArgs);
+template __global__ void param_kernel<kIEEE, 4>(const ParamArgs);
+template __global__ void param_kernel<kIEEE, 8>(const ParamArgs);
+template __global__ void param_kernel<kFAST, 1>(const ParamArgs);
+template __global__ void param_kernel<kFAST, 2>(const ParamArgs);
+template __global__ void param_kernel<kFAST, 4>(const ParamArgs);
+template __global__ void param_kernel<kFAST, 8>(const ParamArgs);
+
+const void* kernel_param(int variant, int P)
+{
+    const bool fast = variant == kFAST;
+    switch (P) {
+    case 1: return fast ? (const void*)param_kernel<kFAST, 1> : (const void*)param_kernel<kIEEE, 1>;
+    case 2: return fast ? (const void*)param_kernel<kFAST, 2> : (const void*)param_kernel<kIEEE, 2>;
+    case 4: return fast ? (const void*)param_kernel<kFAST, 4> : (const void*)param_kernel<kIEEE, 4>;
+    case 8: return fast ? (const void*)param_kernel<kFAST, 8> : (const void*)param_kernel<kIEEE, 8>;
+    }
+    return nullptr;
+}
+
+size_t param_smem_bytes(int P, int n_lig, int n_rows, int n_types, int chunk)
+{
+    const size_t TP = 32u * (size_t)P;
+    const size_t acc = (size_t)(n_lig * 3 + n_rows * n_types * 3) * sizeof(double);
+    size_t off = (acc + 15) & ~size_t(15);
+    off += 13 * TP * sizeof(float);
+    off += (size_t)n_rows * n_types * sizeof(PairG);
+    return off + (size_t)chunk * sizeof(float4);
+}
+
+cudaError_t launch_param_reduce(const double* cta_acc, int n_cta, int n_lig, int n_rows,
+                                int n_types, double* sums, const int* row_type, const float4* ff,
+                                float* lig_grad, float* ff_grad, cudaStream_t s)
+{
+    const int acc_len = n_lig * 3 + n_rows * n_types * 3;
+    int blocks = (acc_len + 255) / 256;
+    param_sum_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, s>>>(cta_acc, n_cta, acc_len, sums);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int outs = n_lig * 3 + n_types;
+    param_finish_kernel<<<(outs + 127) / 128, 128, 0, s>>>(sums, n_lig, n_rows, n_types,
+                                                            row_type, ff, lig_grad, ff_grad);
+    return cudaGetLastError();
+}
+
+}  // namespace bude

@@ -43,6 +43,10 @@ for d, o in zip(decks_np, bude.energies_batched(decks, poses, ppwi=16, block=384
 Q = P.clone()
 E = bude.refine_device(deck, Q, steps=3, step0=0.05)
 assert err(E, D, Q.cpu().numpy()) < 1e-5
+gl, gf = bude.param_grad(deck, P, ppwi=4, block=128, tile=150)
+GL, GF = oracle.param_grad(D, D["poses"])
+assert float(np.abs(gl.cpu().numpy() - GL).max()) <= 1e-4 * max(np.abs(GL).max(), 1)
+assert float(np.abs(gf.cpu().numpy() - GF).max()) <= 1e-4 * max(np.abs(GF).max(), 1)
 print("device checks silent")
 '''
 

@@ -366,3 +366,57 @@ def test_refine_never_raises_energy_and_keeps_rejected_poses():
     for r in ratios:
         ok = any(abs(r - (a * np.log(1.25) + (6 - a) * np.log(0.5))) < 1e-9 for a in range(7))
         assert ok
+
+
+# --- gradients with respect to ligand coordinates and forcefield ------------
+
+def _weighted_energy(D, P, w):
+    return float(np.dot(w, oracle.energies(D, P)))
+
+
+def test_param_grad_ligand_coordinates_match_central_differences():
+    D = _as64(synth.make_deck(30, 6, 150, 6, 10))
+    w = np.random.default_rng(0).uniform(0.5, 1.5, 10)
+    GL, _ = oracle.param_grad(D, D["poses"], w)
+    h = 1e-5
+    scale = max(np.abs(GL).max(), 1.0)
+    for l in range(6):
+        for i in range(3):
+            Dp, Dm = dict(D), dict(D)
+            Dp["lig_xyz"] = D["lig_xyz"].copy()
+            Dm["lig_xyz"] = D["lig_xyz"].copy()
+            Dp["lig_xyz"][l, i] += h
+            Dm["lig_xyz"][l, i] -= h
+            fd = (_weighted_energy(Dp, D["poses"], w) - _weighted_energy(Dm, D["poses"], w)) / (2 * h)
+            assert abs(fd - GL[l, i]) <= 1e-5 * scale, (l, i, fd, GL[l, i])
+
+
+@pytest.mark.parametrize("col,key", [(0, "radius"), (1, "hardness"), (2, "elsc")])
+def test_param_grad_forcefield_matches_central_differences(col, key):
+    D = _as64(synth.make_deck(31, 8, 200, 5, 12))
+    w = np.random.default_rng(1).uniform(0.5, 1.5, 12)
+    _, GF = oracle.param_grad(D, D["poses"], w)
+    h = 1e-6
+    scale = max(np.abs(GF[:, col]).max(), 1.0)
+    for t in range(5):
+        Dp, Dm = dict(D), dict(D)
+        Dp[key] = D[key].copy()
+        Dm[key] = D[key].copy()
+        Dp[key][t] += h
+        Dm[key][t] -= h
+        fd = (_weighted_energy(Dp, D["poses"], w) - _weighted_energy(Dm, D["poses"], w)) / (2 * h)
+        assert abs(fd - GF[t, col]) <= 1e-4 * scale, (key, t, fd, GF[t, col])
+
+
+def test_param_grad_scaling_identities():
+    """Energy is linear in hardness (steric) and quadratic in elsc
+    (electrostatics): sum_t h_t dL/dh_t = L_steric and
+    sum_t q_t dL/dq_t = 2 L_elec (Euler's theorem for homogeneous terms)."""
+    D = _as64(synth.make_deck(32, 8, 200, 6, 9))
+    D["hbtype"] = np.zeros_like(D["hbtype"])          # no desolvation
+    P = D["poses"]
+    _, GF = oracle.param_grad(D, P)
+    L_ster = oracle.energies(dict(D, elsc=np.zeros_like(D["elsc"])), P).sum()
+    L_elec = oracle.energies(dict(D, hardness=np.zeros_like(D["hardness"])), P).sum()
+    assert np.dot(D["hardness"], GF[:, 1]) == pytest.approx(L_ster, rel=1e-10, abs=1e-10)
+    assert np.dot(D["elsc"], GF[:, 2]) == pytest.approx(2 * L_elec, rel=1e-10, abs=1e-10)
