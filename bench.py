@@ -273,6 +273,44 @@ def param_grad_throughput(bude, synth, dev, timed, variant="fast"):
             "kernels_per_call": launches // 5}
 
 
+def hbm_calibration(bude, dev, timed, peak_gbs):
+    """The paper's memory-bound kernels on this GPU: GB/s by Eq. 2 (BabelStream,
+    2^25 and 2^28 elements) and Eq. 1 (seven-point stencil, FP32 L=1024, FP64
+    L=512), against the measured copy bandwidth."""
+    import torch
+    out = {}
+    for dtype, name in ((torch.float32, "f32"), (torch.float64, "f64")):
+        item = torch.tensor([], dtype=dtype).element_size()
+        for n in (1 << 25, 1 << 28):
+            a = torch.full((n,), 0.1, dtype=dtype, device=dev)
+            b = torch.full((n,), 0.2, dtype=dtype, device=dev)
+            c = torch.zeros(n, dtype=dtype, device=dev)
+            d = torch.empty((), dtype=torch.float64, device=dev)
+            ops = {"copy": (lambda: bude.stream_op("copy", a=a, c=c), 2),
+                   "mul": (lambda: bude.stream_op("mul", b=b, c=c, scalar=0.4), 2),
+                   "add": (lambda: bude.stream_op("add", a=a, b=b, c=c), 3),
+                   "triad": (lambda: bude.stream_op("triad", a=a, b=b, c=c, scalar=0.4), 3),
+                   "dot": (lambda: bude.stream_op("dot", a=a, b=b, dot_out=d), 2)}
+            for op, (fn, arrays) in ops.items():
+                ms, _ = timed(fn, 20, 3)
+                gbs = arrays * n * item / (statistics.median(ms) / 1e3) / 1e9
+                out[f"{op}_{name}_2^{n.bit_length() - 1}"] = {
+                    "gb_s": gbs, "frac_of_measured_copy": gbs / peak_gbs}
+            del a, b, c
+        L = 1024 if name == "f32" else 512
+        u = torch.rand((L, L, L), dtype=dtype, device=dev)
+        f = torch.zeros_like(u)
+        ms, _ = timed(lambda: bude.laplacian(u, f, 1.0, 1.0, 1.0, -6.0), 10, 3)
+        fetch = L ** 3 - 8 - 12 * (L - 2)
+        write = (L - 2) ** 3
+        gbs = (fetch + write) * item / (statistics.median(ms) / 1e3) / 1e9
+        out[f"stencil_{name}_L{L}"] = {"gb_s": gbs, "frac_of_measured_copy": gbs / peak_gbs,
+                                        "ms": statistics.median(ms)}
+        del u, f
+        torch.cuda.empty_cache()
+    return out
+
+
 def reference_arm(args):
     """The FP64 oracle as it stands, timed on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -457,6 +495,8 @@ def main():
         line["adjoint"] = adjoint_throughput(bude, synth, tune, dev, timed)
         line["refine"] = refine_throughput(bude, synth, tune, dev, timed)
         line["param_grad"] = param_grad_throughput(bude, synth, dev, timed)
+        line["hbm_calibration"] = hbm_calibration(bude, dev, timed,
+                                                  peaks.get("hbm_gbs", 6800.0))
 
     # CPU-baseline leg: the FP64 oracle on a bounded sample of the same poses.
     # Its sample energies also give each variant's error on that sample.

@@ -247,6 +247,33 @@ BUDE_API int bude_param_grad(bude_deck* deck, const float* poses, int64_t n,
                              const float* weights, float* lig_grad, float* ff_grad,
                              const bude_options* opts, void* stream);
 
+/*
+ * The paper's memory-bound kernels, kept as HBM calibration for this GPU
+ * (Sec. 2.2, Listings 2 and 3; bandwidth metrics Eq. 1 and Eq. 2).
+ *
+ * bude_stream -- one BabelStream operation on n elements of device arrays
+ * (dtype 0 float32, 1 float64; every array 16-byte aligned):
+ *   op 0 copy  c = a        op 1 mul  b = scalar c      op 2 add  c = a + b
+ *   op 3 triad a = b + scalar c                          op 4 dot  *dot_result = sum a b
+ * dot_result is a device double (op 4 only), accumulated in FP64 and reduced
+ * over CTAs in a fixed order through a fixed device array shared by all calls
+ * (dot calls must not overlap on the GPU).  Asynchronous on "stream".
+ */
+BUDE_API int bude_stream(int32_t op, int32_t dtype, void* a, void* b, void* c, double scalar,
+                         int64_t n, double* dot_result, void* stream);
+
+/*
+ * bude_laplacian -- seven-point stencil on an nx x ny x nz grid (index
+ * i*ny*nz + j*nz + k, k fastest), interior points only:
+ *   f[i,j,k] = u[i,j,k] invhxyz2 + (u[i-1,j,k] + u[i+1,j,k]) invhx2
+ *            + (u[i,j-1,k] + u[i,j+1,k]) invhy2 + (u[i,j,k-1] + u[i,j,k+1]) invhz2
+ * Boundary points of f are not written.  u and f are distinct device arrays
+ * of dtype 0 float32 or 1 float64.  Grids with a side below 3 are a no-op.
+ */
+BUDE_API int bude_laplacian(int32_t dtype, const void* u, void* f, int32_t nx, int32_t ny,
+                            int32_t nz, double invhx2, double invhy2, double invhz2,
+                            double invhxyz2, void* stream);
+
 /* Default options the library uses for a variant when a field is zero. */
 BUDE_API int bude_get_default_options(int32_t variant, bude_options* out);
 BUDE_API int bude_set_default_options(const bude_options* opts);

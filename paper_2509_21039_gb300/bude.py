@@ -83,6 +83,9 @@ def load(path: str | None = None):
         "bude_pose_grad": (ci, [vp, vp, i64, vp, vp, ctypes.POINTER(Options), vp]),
         "bude_refine": (ci, [vp, vp, i64, i32, ctypes.c_float, vp, ctypes.POINTER(Options), vp]),
         "bude_param_grad": (ci, [vp, vp, i64, vp, vp, vp, ctypes.POINTER(Options), vp]),
+        "bude_stream": (ci, [i32, i32, vp, vp, vp, ctypes.c_double, i64, vp, vp]),
+        "bude_laplacian": (ci, [i32, vp, vp, i32, i32, i32, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, vp]),
         "bude_get_default_options": (ci, [i32, ctypes.POINTER(Options)]),
         "bude_set_default_options": (ci, [ctypes.POINTER(Options)]),
         "bude_last_launch_count": (i64, []),
@@ -344,6 +347,49 @@ def param_grad(deck: Deck, poses: torch.Tensor, weights: torch.Tensor | None = N
                                 _stream_ptr(stream))
     _check(rc)
     return gl, gf
+
+
+STREAM_OPS = {"copy": 0, "mul": 1, "add": 2, "triad": 3, "dot": 4}
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return 0
+    if t.dtype == torch.float64:
+        return 1
+    raise TypeError("float32 or float64 tensors only")
+
+
+def stream_op(op: str, a=None, b=None, c=None, scalar: float = 0.4, dot_out=None, stream=None):
+    """One BabelStream operation (copy c=a, mul b=s c, add c=a+b, triad
+    a=b+s c, dot) on equal-length contiguous device tensors."""
+    ts = [t for t in (a, b, c) if t is not None]
+    if not ts or any((not t.is_contiguous()) or t.dtype != ts[0].dtype or t.numel() != ts[0].numel()
+                     for t in ts):
+        raise ValueError("contiguous tensors of one dtype and length")
+    code = STREAM_OPS[op]
+    if code == 4 and dot_out is None:
+        dot_out = torch.empty((), dtype=torch.float64, device=ts[0].device)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+    rc = load().bude_stream(code, _dtype_code(ts[0]), ptr(a), ptr(b), ptr(c), float(scalar),
+                            ts[0].numel(), ptr(dot_out), _stream_ptr(stream))
+    _check(rc)
+    return dot_out
+
+
+def laplacian(u: torch.Tensor, f: torch.Tensor, invhx2=1.0, invhy2=1.0, invhz2=1.0,
+              invhxyz2=-6.0, stream=None):
+    """Seven-point stencil of Listing 2 on [nx, ny, nz] tensors (interior of f)."""
+    if u.shape != f.shape or u.dim() != 3 or u.dtype != f.dtype:
+        raise ValueError("u and f: same [nx, ny, nz] shape and dtype")
+    if not (u.is_contiguous() and f.is_contiguous()):
+        raise ValueError("contiguous tensors")
+    nx, ny, nz = u.shape
+    rc = load().bude_laplacian(_dtype_code(u), ctypes.c_void_p(u.data_ptr()),
+                               ctypes.c_void_p(f.data_ptr()), nx, ny, nz, float(invhx2),
+                               float(invhy2), float(invhz2), float(invhxyz2), _stream_ptr(stream))
+    _check(rc)
+    return f
 
 
 class PoseEnergy(torch.autograd.Function):

@@ -323,7 +323,9 @@ int ensure_workspace(double** partial, size_t* pbytes, unsigned** counter, size_
 
 // Device error word of BUDE_DEVICE_CHECKS builds: one per device, looked up
 // once (its host-side symbol is only a stand-in for the device address).
+#ifdef BUDE_DEVICE_CHECKS
 static __device__ unsigned g_device_err;
+#endif
 
 unsigned* device_err_word()
 {
