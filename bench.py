@@ -311,6 +311,29 @@ def hbm_calibration(bude, dev, timed, peak_gbs):
     return out
 
 
+def hartree_fock(bude, synth, dev, timed):
+    """Two-electron Fock build for synthetic helium lattices of 64, 128 and 256
+    atoms with 3 primitives per atom (the paper's Table 4 sizes), FP32
+    integrals with FP64 accumulation and all-FP64, Schwarz threshold 1e-12."""
+    import torch
+    out = {}
+    for n in (64, 128, 256):
+        s = synth.make_he_lattice(11, n, 3)
+        hf = bude.HartreeFock(s["geom"], s["xpnt"], s["coef"], device=dev)
+        D = torch.from_numpy(s["dens"]).to(dev)
+        row = {}
+        for v in ("ieee", "fp64"):
+            reps = 1 if (v == "fp64" and n == 256) else 5
+            ms, _ = timed(lambda: hf.fock(D, tol=1e-12, variant=v), reps, 1)
+            row["fp32_integrals_ms" if v == "ieee" else "fp64_ms"] = statistics.median(ms)
+        G64 = hf.fock(D, tol=1e-12, variant="fp64")
+        G32 = hf.fock(D, tol=1e-12, variant="ieee")
+        row["fp32_vs_fp64_max_rel"] = ((G32 - G64).abs().max() / G64.abs().max()).item()
+        out[f"a={n} ngauss=3"] = row
+        hf.close()
+    return out
+
+
 def reference_arm(args):
     """The FP64 oracle as it stands, timed on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -497,6 +520,7 @@ def main():
         line["param_grad"] = param_grad_throughput(bude, synth, dev, timed)
         line["hbm_calibration"] = hbm_calibration(bude, dev, timed,
                                                   peaks.get("hbm_gbs", 6800.0))
+        line["hartree_fock"] = hartree_fock(bude, synth, dev, timed)
 
     # CPU-baseline leg: the FP64 oracle on a bounded sample of the same poses.
     # Its sample energies also give each variant's error on that sample.

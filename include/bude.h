@@ -274,6 +274,32 @@ BUDE_API int bude_laplacian(int32_t dtype, const void* u, void* f, int32_t nx, i
                             int32_t nz, double invhx2, double invhy2, double invhz2,
                             double invhxyz2, void* stream);
 
+/*
+ * Hartree-Fock two-electron Fock term over s-type Gaussians (the paper's
+ * other compute-bound kernel: Sec. 2.2, Listing 5, Table 4).  Every atom
+ * carries one s function contracted from ngauss normalised primitives
+ * (exponents xpnt, coefficients coef, the same on every atom); geometry in
+ * bohr.  For a symmetric density D the call computes
+ *   G_ij = sum_kl D_kl [ 2 (ij|kl) - (ik|jl) ]
+ * from the unique integrals (i >= j, k >= l, ij >= kl) with the six Fock
+ * updates of Listing 5 (FP64 atomics) and G = F + F^T.  Quartets whose
+ * Schwarz bound sqrt((ij|ij) (kl|kl)) is below schwarz_tol are skipped.
+ *
+ * bude_hf_create: geom [n_atoms][3], xpnt and coef [ngauss] are HOST arrays
+ *   (ngauss 1..8); builds the pair products and Schwarz bounds on the GPU and
+ *   synchronises "stream".
+ * bude_hf_fock: dens and g are device float64 [n][n] (row-major).  variant
+ *   BUDE_FP64 evaluates every integral in FP64; BUDE_FP32_IEEE evaluates the
+ *   primitive integrals in FP32 (GB300's FP64 rate is a small fraction of its
+ *   FP32 rate) and accumulates in FP64.  Calls on one plan must not overlap.
+ */
+typedef struct bude_hf bude_hf;
+BUDE_API int bude_hf_create(int32_t n_atoms, const double* geom, int32_t ngauss,
+                            const double* xpnt, const double* coef, void* stream, bude_hf** out);
+BUDE_API int bude_hf_fock(bude_hf* plan, const double* dens, double* g, double schwarz_tol,
+                          int32_t variant, void* stream);
+BUDE_API int bude_hf_destroy(bude_hf* plan);
+
 /* Default options the library uses for a variant when a field is zero. */
 BUDE_API int bude_get_default_options(int32_t variant, bude_options* out);
 BUDE_API int bude_set_default_options(const bude_options* opts);

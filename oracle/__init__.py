@@ -19,7 +19,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "bude_oracle.c")
+_SRCS = [os.path.join(_HERE, "bude_oracle.c"), os.path.join(_HERE, "hf_oracle.c")]
 _LIB = os.path.join(_HERE, "libbude_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -33,10 +33,10 @@ _CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
 def build(force: bool = False) -> str:
     """Compile ``bude_oracle.c`` into ``libbude_oracle.so`` (gcc, OpenMP)."""
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", *_CFLAGS, _SRC, "-o", tmp, "-lm"], check=True)
+    subprocess.run(["gcc", *_CFLAGS, *_SRCS, "-o", tmp, "-lm"], check=True)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -66,6 +66,14 @@ def _load():
         lib.oracle_pose_grad.argtypes = deck_args + [i64, dp, dp, dp, dp, ci]
         lib.oracle_param_grad.restype = ci
         lib.oracle_param_grad.argtypes = deck_args + [i64, dp, dp, dp, dp]
+        lib.oracle_boys0.restype = cd
+        lib.oracle_boys0.argtypes = [cd]
+        lib.oracle_prim_eri.restype = cd
+        lib.oracle_prim_eri.argtypes = [cd, dp, cd, dp, cd, dp, cd, dp]
+        lib.oracle_eri.restype = cd
+        lib.oracle_eri.argtypes = [ci, dp, dp, dp, dp, dp, dp]
+        lib.oracle_hf_fock_entries.restype = None
+        lib.oracle_hf_fock_entries.argtypes = [ci, dp, ci, dp, dp, dp, ci, ip, ip, dp]
         lib.oracle_max_threads.restype = ci
         lib.oracle_max_threads.argtypes = []
         _lib = lib
@@ -215,3 +223,47 @@ def refine(deck, poses, steps: int, step0: float, grow: float = 1.25, shrink: fl
         G[:, acc] = Gt[:, acc]
         alpha = np.where(acc, alpha * grow, alpha * shrink)
     return P, E, alpha
+
+
+# --- Hartree-Fock two-electron Fock term (s-type Gaussians) -----------------
+
+def boys0(t: float) -> float:
+    """F0(t) = (1/2) sqrt(pi/t) erf(sqrt t), F0(0) = 1."""
+    return float(_load().oracle_boys0(float(t)))
+
+
+def prim_eri(xa, A, xb, B, xc, C, xd, D) -> float:
+    """Normalised primitive two-electron integral (ab|cd)."""
+    v = [np.ascontiguousarray(X, np.float64) for X in (A, B, C, D)]
+    return float(_load().oracle_prim_eri(float(xa), _dptr(v[0]), float(xb), _dptr(v[1]),
+                                         float(xc), _dptr(v[2]), float(xd), _dptr(v[3])))
+
+
+def eri(xpnt, coef, A, B, C, D) -> float:
+    """Contracted (ij|kl) for s functions on centres A, B, C, D."""
+    x = np.ascontiguousarray(xpnt, np.float64)
+    c = np.ascontiguousarray(coef, np.float64)
+    v = [np.ascontiguousarray(X, np.float64) for X in (A, B, C, D)]
+    return float(_load().oracle_eri(len(x), _dptr(x), _dptr(c), *[_dptr(t) for t in v]))
+
+
+def hf_fock_entries(geom, xpnt, coef, dens, rows, cols):
+    """G_ij = sum_kl D_kl [2 (ij|kl) - (ik|jl)] for the listed (i, j)."""
+    g = np.ascontiguousarray(geom, np.float64).reshape(-1, 3)
+    n = g.shape[0]
+    x = np.ascontiguousarray(xpnt, np.float64)
+    c = np.ascontiguousarray(coef, np.float64)
+    d = np.ascontiguousarray(dens, np.float64).reshape(n, n)
+    r = np.ascontiguousarray(rows, np.int32)
+    k = np.ascontiguousarray(cols, np.int32)
+    out = np.zeros(len(r), np.float64)
+    _load().oracle_hf_fock_entries(n, _dptr(g), len(x), _dptr(x), _dptr(c), _dptr(d), len(r),
+                                   _iptr(r), _iptr(k), _dptr(out))
+    return out
+
+
+def hf_fock(geom, xpnt, coef, dens):
+    """The full G matrix by the plain definition (small systems)."""
+    n = np.asarray(geom).reshape(-1, 3).shape[0]
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    return hf_fock_entries(geom, xpnt, coef, dens, ii.ravel(), jj.ravel()).reshape(n, n)

@@ -84,6 +84,9 @@ def load(path: str | None = None):
         "bude_refine": (ci, [vp, vp, i64, i32, ctypes.c_float, vp, ctypes.POINTER(Options), vp]),
         "bude_param_grad": (ci, [vp, vp, i64, vp, vp, vp, ctypes.POINTER(Options), vp]),
         "bude_stream": (ci, [i32, i32, vp, vp, vp, ctypes.c_double, i64, vp, vp]),
+        "bude_hf_create": (ci, [i32, vp, i32, vp, vp, vp, ctypes.POINTER(vp)]),
+        "bude_hf_fock": (ci, [vp, vp, vp, ctypes.c_double, i32, vp]),
+        "bude_hf_destroy": (ci, [vp]),
         "bude_laplacian": (ci, [i32, vp, vp, i32, i32, i32, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_double, vp]),
         "bude_get_default_options": (ci, [i32, ctypes.POINTER(Options)]),
@@ -390,6 +393,50 @@ def laplacian(u: torch.Tensor, f: torch.Tensor, invhx2=1.0, invhy2=1.0, invhz2=1
                                float(invhy2), float(invhz2), float(invhxyz2), _stream_ptr(stream))
     _check(rc)
     return f
+
+
+class HartreeFock:
+    """Two-electron Fock term G_ij = sum_kl D_kl [2 (ij|kl) - (ik|jl)] over
+    one contracted s function per atom (bude_hf_create / bude_hf_fock)."""
+
+    def __init__(self, geom, xpnt, coef, device=None, stream=None):
+        lib = load()
+        g = np.ascontiguousarray(geom, np.float64).reshape(-1, 3)
+        x = np.ascontiguousarray(xpnt, np.float64)
+        c = np.ascontiguousarray(coef, np.float64)
+        self.n = g.shape[0]
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib.bude_hf_create(self.n, g.ctypes.data_as(ctypes.c_void_p), len(x),
+                                    x.ctypes.data_as(ctypes.c_void_p),
+                                    c.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream),
+                                    ctypes.byref(h))
+        _check(rc)
+        self._h = h
+
+    def fock(self, dens: torch.Tensor, tol: float = 1e-12, variant="fp64", out=None, stream=None):
+        if dens.shape != (self.n, self.n) or dens.dtype != torch.float64 or not dens.is_contiguous():
+            raise ValueError("dens must be a contiguous float64 [n, n] tensor")
+        out = torch.empty_like(dens) if out is None else out
+        v = VARIANTS[variant] if isinstance(variant, str) else variant
+        rc = load().bude_hf_fock(self._h, ctypes.c_void_p(dens.data_ptr()),
+                                 ctypes.c_void_p(out.data_ptr()), float(tol), v,
+                                 _stream_ptr(stream))
+        _check(rc)
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().bude_hf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class PoseEnergy(torch.autograd.Function):

@@ -1,0 +1,299 @@
+// Two-electron part of the Hartree-Fock Fock matrix over s-type Gaussians
+// (arxiv 2509.21039, Sec. 2.2, Listing 5; Table 4), written for GB300.
+//
+// G_ij = sum_kl D_kl [2 (ij|kl) - (ik|jl)] is built from the unique integrals
+// (ij|kl), i >= j, k >= l, ij >= kl: each adds, weighted by its degeneracy
+// (1/2 for i = j, for k = l and for ij = kl),
+//   F_ij += 4 D_kl v   F_kl += 4 D_ij v
+//   F_ik -= D_jl v     F_il -= D_jk v     F_jk -= D_il v     F_jl -= D_ik v
+// (the six updates of Listing 5), and G = F + F^T.  Per plan the kernel set
+// precomputes, for every atom pair and primitive pair, the Gaussian product
+// p = x_a + x_b, P = (x_a A + x_b B)/p and K = c_a c_b N_a N_b
+// exp(-x_a x_b |A-B|^2/p), and the Schwarz bound Q_ij = sqrt((ij|ij)); a
+// quartet with Q_ij Q_kl below the caller's threshold is skipped.  Primitive
+// quartets then cost
+//   (ab|cd) = K_ab K_cd 2 pi^(5/2) / (p q sqrt(p+q)) F0(p q / (p+q) |P-Q|^2)
+// with F0(t) = sqrt(pi/t) erf(sqrt t) / 2.  GB300's FP64 units are a small
+// fraction of its FP32 ones, so besides the FP64 kernel there is one that
+// evaluates the primitive integrals in FP32 and accumulates the Fock matrix
+// in FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "bude_internal.h"
+
+namespace bude {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct HfPlanDev {
+    int n, ng;
+    long long m;          // unique pairs n(n+1)/2
+    const double4_32a* pq;    // [m][ng*ng] {Px, Py, Pz, p}
+    const double* kp;     // [m][ng*ng] K
+    const float4* pqf;    // FP32 copies
+    const float* kpf;
+    const double* schwarz;  // [m]
+};
+
+__device__ __forceinline__ void pair_of(long long ij, int* i, int* j)
+{
+    long long a = (long long)((sqrt(8.0 * (double)ij + 1.0) - 1.0) * 0.5);
+    while (a * (a + 1) / 2 > ij) --a;
+    while ((a + 1) * (a + 2) / 2 <= ij) ++a;
+    *i = (int)a;
+    *j = (int)(ij - a * (a + 1) / 2);
+}
+
+// Gaussian products of every atom pair (i >= j) and primitive pair.
+__global__ void hf_pairs_kernel(int n, int ng, const double* __restrict__ geom,
+                                const double* __restrict__ xpnt, const double* __restrict__ coef,
+                                double4_32a* __restrict__ pq, double* __restrict__ kp,
+                                float4* __restrict__ pqf, float* __restrict__ kpf)
+{
+    const long long m = (long long)n * (n + 1) / 2;
+    const int g2 = ng * ng;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m * g2;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long ij = e / g2;
+        const int ab = (int)(e % g2), a = ab / ng, b = ab % ng;
+        int i, j;
+        pair_of(ij, &i, &j);
+        const double xa = xpnt[a], xb = xpnt[b], p = xa + xb;
+        double r2 = 0.0, P[3];
+        for (int d = 0; d < 3; ++d) {
+            const double A = geom[3 * i + d], B = geom[3 * j + d];
+            r2 += (A - B) * (A - B);
+            P[d] = (xa * A + xb * B) / p;
+        }
+        const double na = pow(2.0 * xa / kPi, 0.75), nb = pow(2.0 * xb / kPi, 0.75);
+        const double K = coef[a] * coef[b] * na * nb * exp(-xa * xb * r2 / p);
+        pq[e] = make_double4_32a(P[0], P[1], P[2], p);
+        kp[e] = K;
+        pqf[e] = make_float4((float)P[0], (float)P[1], (float)P[2], (float)p);
+        kpf[e] = (float)K;
+    }
+}
+
+__device__ __forceinline__ double boys0(double t)
+{
+    if (t < 1e-10) return 1.0 - t / 3.0;
+    const double st = sqrt(t);
+    return 0.5 * sqrt(kPi / t) * erf(st);
+}
+__device__ __forceinline__ float boys0f(float t)
+{
+    if (t < 1e-5f) return 1.0f - t / 3.0f;
+    const float st = sqrtf(t);
+    return 0.5f * sqrtf((float)kPi / t) * erff(st);
+}
+
+// Contracted (ij|kl) from the two pairs' primitive products.
+__device__ double contracted_f64(const HfPlanDev& P, long long ij, long long kl)
+{
+    const int g2 = P.ng * P.ng;
+    const double4_32a* A = P.pq + ij * g2;
+    const double4_32a* C = P.pq + kl * g2;
+    const double* KA = P.kp + ij * g2;
+    const double* KC = P.kp + kl * g2;
+    double v = 0.0;
+    for (int ab = 0; ab < g2; ++ab) {
+        const double4_32a a = A[ab];
+        const double ka = KA[ab];
+        for (int cd = 0; cd < g2; ++cd) {
+            const double4_32a c = C[cd];
+            const double dx = a.x - c.x, dy = a.y - c.y, dz = a.z - c.z;
+            const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+            const double pq = a.w * c.w, s = a.w + c.w;
+            v += ka * KC[cd] * (2.0 * 17.493418327624862 /* pi^(5/2) */) / (pq * sqrt(s)) *
+                 boys0(pq / s * r2);
+        }
+    }
+    return v;
+}
+
+__device__ float contracted_f32(const HfPlanDev& P, long long ij, long long kl)
+{
+    const int g2 = P.ng * P.ng;
+    const float4* A = P.pqf + ij * g2;
+    const float4* C = P.pqf + kl * g2;
+    const float* KA = P.kpf + ij * g2;
+    const float* KC = P.kpf + kl * g2;
+    float v = 0.f;
+    for (int ab = 0; ab < g2; ++ab) {
+        const float4 a = A[ab];
+        const float ka = KA[ab];
+        for (int cd = 0; cd < g2; ++cd) {
+            const float4 c = C[cd];
+            const float dx = a.x - c.x, dy = a.y - c.y, dz = a.z - c.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float pq = a.w * c.w, s = a.w + c.w;
+            v = fmaf(ka * KC[cd] * (float)(2.0 * 17.493418327624862) / (pq * sqrtf(s)),
+                     boys0f(pq / s * r2), v);
+        }
+    }
+    return v;
+}
+
+// Schwarz bounds Q_ij = sqrt((ij|ij)) in FP64.
+__global__ void hf_schwarz_kernel(const HfPlanDev P, double* __restrict__ q)
+{
+    for (long long ij = blockIdx.x * (long long)blockDim.x + threadIdx.x; ij < P.m;
+         ij += (long long)gridDim.x * blockDim.x)
+        q[ij] = sqrt(fabs(contracted_f64(P, ij, ij)));
+}
+
+// One thread per unique quartet (IJ >= KL), grid-stride.
+template <bool F32>
+__global__ void hf_fock_kernel(const HfPlanDev P, const double* __restrict__ D,
+                               double* __restrict__ F, double tol)
+{
+    const long long nq = P.m * (P.m + 1) / 2;
+    const int n = P.n;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
+         q += (long long)gridDim.x * blockDim.x) {
+        int IJ_, KL_;
+        pair_of(q, &IJ_, &KL_);
+        const long long IJ = IJ_, KL = KL_;
+        if (P.schwarz[IJ] * P.schwarz[KL] < tol) continue;
+        int i, j, k, l;
+        pair_of(IJ, &i, &j);
+        pair_of(KL, &k, &l);
+        double v = F32 ? (double)contracted_f32(P, IJ, KL) : contracted_f64(P, IJ, KL);
+        if (i == j) v *= 0.5;
+        if (k == l) v *= 0.5;
+        if (IJ == KL) v *= 0.5;
+        atomicAdd(F + (size_t)i * n + j, 4.0 * D[(size_t)k * n + l] * v);
+        atomicAdd(F + (size_t)k * n + l, 4.0 * D[(size_t)i * n + j] * v);
+        atomicAdd(F + (size_t)i * n + k, -D[(size_t)j * n + l] * v);
+        atomicAdd(F + (size_t)i * n + l, -D[(size_t)j * n + k] * v);
+        atomicAdd(F + (size_t)j * n + k, -D[(size_t)i * n + l] * v);
+        atomicAdd(F + (size_t)j * n + l, -D[(size_t)i * n + k] * v);
+    }
+}
+
+// G = F + F^T
+__global__ void hf_symmetrise_kernel(const double* __restrict__ F, double* __restrict__ G, int n)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        G[e] = F[(size_t)i * n + j] + F[(size_t)j * n + i];
+    }
+}
+
+}  // namespace bude
+
+using namespace bude;
+
+struct bude_hf {
+    int device = 0;
+    int n = 0, ng = 0;
+    long long m = 0;
+    double* geom = nullptr;
+    double* xc = nullptr;  // xpnt[ng], coef[ng]
+    double4_32a* pq = nullptr;
+    double* kp = nullptr;
+    float4* pqf = nullptr;
+    float* kpf = nullptr;
+    double* schwarz = nullptr;
+    double* fock = nullptr;  // [n][n] accumulation buffer
+    HfPlanDev view() const
+    {
+        HfPlanDev v;
+        v.n = n;
+        v.ng = ng;
+        v.m = m;
+        v.pq = pq;
+        v.kp = kp;
+        v.pqf = pqf;
+        v.kpf = kpf;
+        v.schwarz = schwarz;
+        return v;
+    }
+};
+
+extern "C" BUDE_API int bude_hf_destroy(bude_hf* h)
+{
+    if (!h) return BUDE_OK;
+    cudaDeviceSynchronize();
+    cudaFree(h->geom);
+    cudaFree(h->xc);
+    cudaFree(h->pq);
+    cudaFree(h->kp);
+    cudaFree(h->pqf);
+    cudaFree(h->kpf);
+    cudaFree(h->schwarz);
+    cudaFree(h->fock);
+    delete h;
+    return BUDE_OK;
+}
+
+extern "C" BUDE_API int bude_hf_create(int32_t n_atoms, const double* geom, int32_t ngauss,
+                                       const double* xpnt, const double* coef, void* stream,
+                                       bude_hf** out)
+{
+    if (!out) return BUDE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_atoms < 1 || ngauss < 1 || ngauss > 8 || !geom || !xpnt || !coef)
+        return BUDE_ERR_INVALID_ARG;
+    for (int a = 0; a < ngauss; ++a)
+        if (!(xpnt[a] > 0.0) || !std::isfinite(xpnt[a]) || !std::isfinite(coef[a]))
+            return BUDE_ERR_INVALID_ARG;
+    for (long long e = 0; e < 3ll * n_atoms; ++e)
+        if (!std::isfinite(geom[e])) return BUDE_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    bude_hf* h = new bude_hf;
+    cudaGetDevice(&h->device);
+    h->n = n_atoms;
+    h->ng = ngauss;
+    h->m = (long long)n_atoms * (n_atoms + 1) / 2;
+    const size_t e = (size_t)h->m * ngauss * ngauss;
+    auto bail = [&](int code) { bude_hf_destroy(h); return code; };
+    if (cudaMalloc((void**)&h->geom, 3 * sizeof(double) * n_atoms) ||
+        cudaMalloc((void**)&h->xc, 2 * sizeof(double) * ngauss) ||
+        cudaMalloc((void**)&h->pq, e * sizeof(double4_32a)) ||
+        cudaMalloc((void**)&h->kp, e * sizeof(double)) ||
+        cudaMalloc((void**)&h->pqf, e * sizeof(float4)) ||
+        cudaMalloc((void**)&h->kpf, e * sizeof(float)) ||
+        cudaMalloc((void**)&h->schwarz, (size_t)h->m * sizeof(double)) ||
+        cudaMalloc((void**)&h->fock, (size_t)n_atoms * n_atoms * sizeof(double)))
+        return bail(BUDE_ERR_OOM);
+    // host inputs: copied synchronously (plan creation is not on the hot path)
+    if (cudaMemcpy(h->geom, geom, 3 * sizeof(double) * n_atoms, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(h->xc, xpnt, sizeof(double) * ngauss, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(h->xc + ngauss, coef, sizeof(double) * ngauss, cudaMemcpyHostToDevice))
+        return bail(BUDE_ERR_CUDA);
+    const long long blocks = std::min<long long>(4096, ((long long)e + 255) / 256);
+    hf_pairs_kernel<<<(unsigned)std::max(1ll, blocks), 256, 0, s>>>(
+        n_atoms, ngauss, h->geom, h->xc, h->xc + ngauss, h->pq, h->kp, h->pqf, h->kpf);
+    const long long sb = std::min<long long>(4096, (h->m + 127) / 128);
+    hf_schwarz_kernel<<<(unsigned)std::max(1ll, sb), 128, 0, s>>>(h->view(), h->schwarz);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return bail(BUDE_ERR_CUDA);
+    *out = h;
+    return BUDE_OK;
+}
+
+extern "C" BUDE_API int bude_hf_fock(bude_hf* h, const double* dens, double* g, double tol,
+                                     int32_t variant, void* stream)
+{
+    if (!h || !dens || !g || tol < 0.0 || !std::isfinite(tol)) return BUDE_ERR_INVALID_ARG;
+    if (variant != BUDE_FP64 && variant != BUDE_FP32_IEEE) return BUDE_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nn = (size_t)h->n * h->n;
+    if (cudaMemsetAsync(h->fock, 0, nn * sizeof(double), s) != cudaSuccess) return BUDE_ERR_CUDA;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long nq = h->m * (h->m + 1) / 2;
+    const long long blocks = std::max(1ll, std::min<long long>((long long)sms * 16, (nq + 127) / 128));
+    if (variant == BUDE_FP64)
+        hf_fock_kernel<false><<<(unsigned)blocks, 128, 0, s>>>(h->view(), dens, h->fock, tol);
+    else
+        hf_fock_kernel<true><<<(unsigned)blocks, 128, 0, s>>>(h->view(), dens, h->fock, tol);
+    const long long sb = std::max(1ll, std::min<long long>(4096, ((long long)nn + 255) / 256));
+    hf_symmetrise_kernel<<<(unsigned)sb, 256, 0, s>>>(h->fock, g, h->n);
+    return cudaGetLastError() == cudaSuccess ? BUDE_OK : BUDE_ERR_CUDA;
+}

@@ -78,3 +78,22 @@ def make_batched(seed: int, count: int = 64, n_types: int = 34, **ranges):
 SMALL = dict(n_lig=26, n_pro=938, n_types=34, n_poses=4096)      # 26 x 938 x 4096, seed 0
 FULL = dict(n_lig=64, n_pro=2672, n_types=34, n_poses=65536)     # 64 x 2672 x 65536
 GRAD = dict(n_lig=64, n_pro=2672, n_types=34, n_poses=16384)     # pose-gradient deck
+
+
+def make_he_lattice(seed, n_atoms: int, ngauss: int = 3, spacing: float = 3.0):
+    """Synthetic helium-like system for the Hartree-Fock Fock build: atoms on
+    a simple cubic lattice (``spacing`` bohr, jittered by U[-0.2, 0.2]), one
+    s function per atom contracted from ``ngauss`` primitives with exponents
+    log-uniform in [0.3, 7] and coefficients U[0.1, 0.6], and a smooth
+    symmetric density D_ij = 0.5 exp(-|R_i - R_j|^2 / 8) (float64 arrays).
+    Draw order: jitter, exponents, coefficients."""
+    rng = np.random.default_rng(seed)
+    side = int(math.ceil(n_atoms ** (1.0 / 3.0)))
+    grid = np.array([(i, j, k) for i in range(side) for j in range(side)
+                     for k in range(side)][:n_atoms], np.float64) * spacing
+    geom = grid + rng.uniform(-0.2, 0.2, size=grid.shape)
+    xpnt = np.sort(np.exp(rng.uniform(math.log(0.3), math.log(7.0), size=ngauss)))[::-1].copy()
+    coef = rng.uniform(0.1, 0.6, size=ngauss)
+    d2 = ((geom[:, None, :] - geom[None, :, :]) ** 2).sum(-1)
+    dens = 0.5 * np.exp(-d2 / 8.0)
+    return dict(geom=geom, xpnt=xpnt, coef=coef, dens=dens)

@@ -1,0 +1,63 @@
+"""Hartree-Fock two-electron Fock term on the GPU against the oracle's plain
+sum G_ij = sum_kl D_kl [2 (ij|kl) - (ik|jl)] (oracle pinned in
+test_hf_oracle.py).  FP64 gate 1e-11 of max|G| (atomic summation order);
+FP32-integral variant 1e-5 (primitive integrals rounded to FP32)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_21039_gb300 import bude, synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+GATE = {"fp64": 1e-11, "ieee": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2509_21039_gb300 import build
+    build.build()
+    bude.load()
+
+
+@pytest.mark.parametrize("n,ng", [(1, 3), (2, 1), (5, 3), (9, 2), (14, 3)])
+@pytest.mark.parametrize("variant", ["fp64", "ieee"])
+def test_fock_matches_oracle(n, ng, variant):
+    s = synth.make_he_lattice(n, n, ng)
+    G_ref = oracle.hf_fock(s["geom"], s["xpnt"], s["coef"], s["dens"])
+    hf = bude.HartreeFock(s["geom"], s["xpnt"], s["coef"], device=DEV)
+    G = hf.fock(torch.from_numpy(s["dens"]).to(DEV), tol=0.0, variant=variant).cpu().numpy()
+    scale = max(np.abs(G_ref).max(), 1e-30)
+    assert np.abs(G - G_ref).max() / scale <= GATE[variant]
+    np.testing.assert_array_equal(G, G.T)
+
+
+def test_fock_sampled_entries_64_atoms_with_screening():
+    s = synth.make_he_lattice(7, 64, 3)
+    hf = bude.HartreeFock(s["geom"], s["xpnt"], s["coef"], device=DEV)
+    D = torch.from_numpy(s["dens"]).to(DEV)
+    G = hf.fock(D, tol=1e-12).cpu().numpy()
+    G32 = hf.fock(D, tol=1e-12, variant="ieee").cpu().numpy()
+    rng = np.random.default_rng(0)
+    rows = rng.integers(0, 64, 16)
+    cols = rng.integers(0, 64, 16)
+    ref = oracle.hf_fock_entries(s["geom"], s["xpnt"], s["coef"], s["dens"], rows, cols)
+    scale = np.abs(G).max()
+    # skipped quartets are bounded by the Schwarz threshold
+    assert np.abs(G[rows, cols] - ref).max() <= 1e-9 * scale
+    assert np.abs(G32[rows, cols] - ref).max() <= 1e-5 * scale
+
+
+def test_fock_linear_in_density_and_rejects_bad_input():
+    s = synth.make_he_lattice(8, 6, 3)
+    hf = bude.HartreeFock(s["geom"], s["xpnt"], s["coef"], device=DEV)
+    D = torch.from_numpy(s["dens"]).to(DEV)
+    G1 = hf.fock(D, tol=0.0)
+    G2 = hf.fock(3.0 * D, tol=0.0)
+    torch.testing.assert_close(G2, 3.0 * G1, rtol=1e-12, atol=1e-14)
+    assert torch.all(hf.fock(torch.zeros_like(D), tol=0.0) == 0)
+    with pytest.raises(bude.BudeError):
+        hf.fock(D, variant="fast")
+    with pytest.raises(bude.BudeError):
+        bude.HartreeFock(s["geom"], -s["xpnt"], s["coef"], device=DEV)
