@@ -130,6 +130,12 @@ size_t record_bytes(int variant, bool G, int P)
 // Bytes of one staged protein atom in shared memory.
 size_t protein_bytes(int variant, int P, bool G) { return packed(variant, P, G) ? 32 : 16; }
 
+// Per-chunk run-end table of the packed energy kernels: one int per type.
+size_t run_bytes(int variant, int P, bool G, int n_types)
+{
+    return (packed(variant, P, G) && !G) ? (((size_t)n_types * 4 + 15) & ~size_t(15)) : 0;
+}
+
 // Dynamic shared memory of pose_kernel before the pair table and protein
 // chunk: max(transforms, warp partials) + final sums.  Mirrors the kernel.
 size_t smem_fixed(int variant, int P, bool G, int block)
@@ -194,7 +200,8 @@ struct InstanceShape {
 int chunk_for(const InstanceShape& s, const Resolved& r, bool G, size_t budget)
 {
     const size_t fixed = smem_fixed(r.variant, r.P, G, r.block);
-    const size_t table = (size_t)s.n_rows * s.n_types * record_bytes(r.variant, G, r.P);
+    const size_t table = (size_t)s.n_rows * s.n_types * record_bytes(r.variant, G, r.P) +
+                         run_bytes(r.variant, r.P, G, s.n_types);
     const size_t pb = protein_bytes(r.variant, r.P, G);
     if (fixed + table + pb * 32 > budget) return -1;
     size_t cap = (budget - fixed - table) / pb;
@@ -258,7 +265,8 @@ int make_plan(const std::vector<const bude_deck*>& decks, const std::vector<cons
         tiles += nt;
         const size_t sm = smem_fixed(r.variant, r.P, G, r.block) +
                           (size_t)d->n_rows * d->n_types * record_bytes(r.variant, G, r.P) +
-                          protein_bytes(r.variant, r.P, G) * (size_t)ch;
+                          protein_bytes(r.variant, r.P, G) * (size_t)ch +
+                          run_bytes(r.variant, r.P, G, d->n_types);
         smem_max = std::max(smem_max, sm);
         pl->inst.push_back(I);
     }
