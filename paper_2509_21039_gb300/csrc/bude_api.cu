@@ -130,10 +130,10 @@ size_t record_bytes(int variant, bool G, int P)
 // Bytes of one staged protein atom in shared memory.
 size_t protein_bytes(int variant, int P, bool G) { return packed(variant, P, G) ? 32 : 16; }
 
-// Per-chunk run-end table of the packed energy kernels: one int per type.
+// Per-chunk run-end table of the packed kernels: one int per type.
 size_t run_bytes(int variant, int P, bool G, int n_types)
 {
-    return (packed(variant, P, G) && !G) ? (((size_t)n_types * 4 + 15) & ~size_t(15)) : 0;
+    return packed(variant, P, G) ? (((size_t)n_types * 4 + 15) & ~size_t(15)) : 0;
 }
 
 // Dynamic shared memory of pose_kernel before the pair table and protein
