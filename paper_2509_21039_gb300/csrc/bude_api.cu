@@ -246,8 +246,11 @@ int make_plan(const std::vector<const bude_deck*>& decks, const std::vector<cons
         memset(&I, 0, sizeof I);
         I.pro = d->pro;
         I.lig = d->lig;
+        // packed kernels stage their records from the adjoint table, which
+        // also holds the steric factors sqrt|H|/R and sqrt|H|
         I.pair = r.variant == BUDE_FP64 ? (const void*)d->tabD
-                                        : (G ? (const void*)d->tabG : (const void*)d->tabF);
+                 : (G || packed(r.variant, r.P, G)) ? (const void*)d->tabG
+                                                    : (const void*)d->tabF;
         I.poses = poses[i];
         I.out = out[i];
         I.grad = G ? grad[i] : nullptr;

@@ -110,7 +110,10 @@ __global__ void build_tables_kernel(const float4* __restrict__ lig_src, int n_li
         g.ae0 = (float)(-2.0 / kDE * d.ke0);
         g.ad1 = (float)(-3.0 / kDD * d.kd1);
         g.ad0 = (float)(-2.0 / kDD * d.kd0);
-        g.pad0 = g.pad1 = g.pad2 = 0.f;
+        const double sh = sqrt(fabs(H));
+        g.sa = (float)(sh * d.inv_r);
+        g.sb = (float)sh;
+        g.pad = 0.f;
         tabG[i] = g;
     }
 }
