@@ -130,10 +130,10 @@ size_t record_bytes(int variant, bool G, int P)
 // Bytes of one staged protein atom in shared memory.
 size_t protein_bytes(int variant, int P, bool G) { return packed(variant, P, G) ? 32 : 16; }
 
-// Per-chunk run-end table of the packed kernels: one int per type.
-size_t run_bytes(int variant, int P, bool G, int n_types)
+// Per-chunk run table and ligand-row cost prefix of the packed kernels.
+size_t run_bytes(int variant, int P, bool G, int n_types, int n_lig)
 {
-    return packed(variant, P, G) ? (((size_t)n_types * 4 + 15) & ~size_t(15)) : 0;
+    return packed(variant, P, G) ? run_area_bytes(n_types, n_lig) : 0;
 }
 
 // Dynamic shared memory of pose_kernel before the pair table and protein
@@ -201,7 +201,7 @@ int chunk_for(const InstanceShape& s, const Resolved& r, bool G, size_t budget)
 {
     const size_t fixed = smem_fixed(r.variant, r.P, G, r.block);
     const size_t table = (size_t)s.n_rows * s.n_types * record_bytes(r.variant, G, r.P) +
-                         run_bytes(r.variant, r.P, G, s.n_types);
+                         run_bytes(r.variant, r.P, G, s.n_types, s.n_lig);
     const size_t pb = protein_bytes(r.variant, r.P, G);
     if (fixed + table + pb * 32 > budget) return -1;
     size_t cap = (budget - fixed - table) / pb;
@@ -269,7 +269,7 @@ int make_plan(const std::vector<const bude_deck*>& decks, const std::vector<cons
         const size_t sm = smem_fixed(r.variant, r.P, G, r.block) +
                           (size_t)d->n_rows * d->n_types * record_bytes(r.variant, G, r.P) +
                           protein_bytes(r.variant, r.P, G) * (size_t)ch +
-                          run_bytes(r.variant, r.P, G, d->n_types);
+                          run_bytes(r.variant, r.P, G, d->n_types, d->n_lig);
         smem_max = std::max(smem_max, sm);
         pl->inst.push_back(I);
     }
