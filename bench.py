@@ -39,19 +39,41 @@ FP32_LANES_PER_SM = 128
 
 # DRAM traffic of one full-size FAST launch, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, mean of 9 launches; see
-# profiles/pose_kernel_fast_full_64x2672x65536_launches.md).  Reported only
+# profiles/pose_kernel_fast_64x2672x65536_launches.md).  Reported only
 # while the kernel source and the launch shape are the ones that were
 # measured.
-MEASURED_TRAFFIC = {"kernel_sha256_16": "ce30056764a620a3", "variant": "fast", "ppwi": 16,
-                    "block": 384, "bytes": 1824711.0}
+MEASURED_TRAFFIC = {"kernel_sha256_16": "6a27298a906b8fa3", "variant": "fast", "ppwi": 8,
+                    "block": 512, "bytes": 1844935.0}
+
+# FP32 FLOPs the kernel executes per pose-pair on the full deck, from ncu's
+# per-opcode thread-instruction counters of the same launch (FADD, FMUL 1;
+# FFMA, FADD2, FMUL2 2; FFMA2 4), per variant, for the kernel source with
+# this hash.  Fewer than Eq. 3's 30: zero desolvation runs are skipped, and
+# FAST rearranges the squared distance and the steric term.
+MEASURED_EXECUTED = {"kernel_sha256_16": "6a27298a906b8fa3",
+                     "flop_per_pair": {"fast": 21.25, "ieee": 29.25, "comp": 29.24}}
 
 
-def measured_traffic(variant, ppwi, block, n_poses):
+def kernel_sha():
     import hashlib
     src = os.path.join(ROOT, "paper_2509_21039_gb300", "csrc", "bude_kernels.cuh")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     except OSError:
+        return None
+
+
+def measured_executed(variant):
+    """Executed FLOP per pose-pair of the current kernel, or None if unmeasured."""
+    m = MEASURED_EXECUTED
+    if kernel_sha() != m["kernel_sha256_16"]:
+        return None
+    return m["flop_per_pair"].get(variant)
+
+
+def measured_traffic(variant, ppwi, block, n_poses):
+    sha = kernel_sha()
+    if sha is None:
         return None
     m = MEASURED_TRAFFIC
     if (sha, variant, ppwi, block, n_poses) != (m["kernel_sha256_16"], m["variant"], m["ppwi"],
@@ -344,10 +366,16 @@ def reference_arm(args):
     oracle.build()
     D = synth.make_deck(1, **FULL)
     cores = oracle.max_threads()
-    # per step: a bounded sample of the poses, sized so the whole run stays short
-    per_step = max(4 * cores, 64)
+    # per step: a bounded sample of the poses, sized from a calibration call so
+    # that warm-up plus timed steps take about a minute in all
+    k = max(4 * cores, 64)
+    t0 = time.perf_counter()
+    oracle.energies(D, D["poses"][:, :k], n_threads=-1)
+    rate = k / max(time.perf_counter() - t0, 1e-6)
+    budget = min(0.5, 60.0 / max(args.steps + args.warmup, 1))
+    per_step = int(min(FULL["n_poses"] // 2, max(k, rate * budget)))
     for _ in range(args.warmup):
-        oracle.energies(D, D["poses"][:, :cores], n_threads=-1)
+        oracle.energies(D, D["poses"][:, :per_step], n_threads=-1)
     times = []
     for s in range(args.steps):
         lo = (s * per_step) % (FULL["n_poses"] - per_step)
@@ -485,10 +513,13 @@ def main():
         "flop_count": "Eq. 3 in the many-poses limit: 28 + nlig (18 + 30 npro) per pose",
         "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz",
         "eq3_tflops_at_ppwi": eq3_flops(shape["n_lig"], shape["n_pro"], n, ppwi) / (ms_mean / 1e3) / 1e12,
-        # FLOPs the FP32 kernel executes per pose-pair: FADD 3, FMUL 1 + FFMA 2
-        # (distance), steric 5, two switches 7 each (FFMA = 2) = 27, plus a root
-        "executed_tflops": 27.0 * shape["n_lig"] * shape["n_pro"] * n / (ms_mean / 1e3) / 1e12,
     }
+    xf = measured_executed(args.variant)
+    if xf is not None:
+        # FLOPs the kernel executes (ncu opcode counters), not Eq. 3's count
+        roofline["executed_flop_per_pair"] = xf
+        roofline["executed_tflops"] = xf * shape["n_lig"] * shape["n_pro"] * n / (ms_mean / 1e3) / 1e12
+        roofline["executed_frac"] = roofline["executed_tflops"] / peak_max
     if clocks:
         clk_peak = sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12
         roofline["frac_at_measured_clock"] = achieved / clk_peak
@@ -561,6 +592,10 @@ def main():
                                    "rel_err_max": float(rel.max()),
                                    "error_sample_poses": int(len(rf)),
                                    "timed_poses": int(npos)}
+                xv = measured_executed(vname)
+                if xv is not None:
+                    variants[vname]["executed_frac"] = (xv * shape["n_lig"] * shape["n_pro"] * npos
+                                                        / t / 1e12 / peak_max)
             line["variants"] = variants
     print(json.dumps(line), flush=True)
     if world > 1:
