@@ -310,6 +310,21 @@ BUDE_API int64_t bude_last_launch_count(void);
 BUDE_API const char* bude_status_string(int status);
 BUDE_API const char* bude_last_error(void);
 
+/*
+ * Host-side fault injection for tests (no paper counterpart).  After
+ * bude_debug_fail_alloc(n) with n > 0, the n-th device allocation the library
+ * makes from then on fails as if the device were out of memory: the call that
+ * makes it returns BUDE_ERR_OOM and must release whatever it had taken.  The
+ * injection is one-shot and process-wide; n = 0 disarms it, n < 0 returns
+ * BUDE_ERR_INVALID_ARG.  Nothing is allocated, freed or launched and no CUDA
+ * call is made for the injected failure, so the CUDA context stays healthy.
+ * bude_debug_pending_fail_alloc() returns how many allocations remain before
+ * the injected failure (0 when disarmed): a call that allocates nothing leaves
+ * it unchanged.
+ */
+BUDE_API int bude_debug_fail_alloc(int32_t n);
+BUDE_API int32_t bude_debug_pending_fail_alloc(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,6 +95,8 @@ def load(path: str | None = None):
         "bude_selfcheck_sqrt": (ci, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32), vp]),
         "bude_status_string": (ctypes.c_char_p, [ci]),
         "bude_last_error": (ctypes.c_char_p, []),
+        "bude_debug_fail_alloc": (ci, [i32]),
+        "bude_debug_pending_fail_alloc": (i32, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -130,6 +132,17 @@ def selfcheck_sqrt(stream=None):
     first = ctypes.c_uint32()
     _check(load().bude_selfcheck_sqrt(ctypes.byref(n), ctypes.byref(first), _stream_ptr(stream)))
     return n.value, first.value
+
+
+def debug_fail_alloc(n: int) -> None:
+    """Make the n-th device allocation of the library from now on fail with
+    BUDE_ERR_OOM (host-side fault injection for tests; 0 disarms)."""
+    _check(load().bude_debug_fail_alloc(int(n)))
+
+
+def debug_pending_fail_alloc() -> int:
+    """Allocations left before the injected failure (0 when disarmed)."""
+    return int(load().bude_debug_pending_fail_alloc())
 
 
 def launch_count() -> int:

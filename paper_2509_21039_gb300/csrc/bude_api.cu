@@ -6,6 +6,7 @@
 // the shared-memory carve-up -- happens here; all arithmetic of the path runs
 // in the kernels.
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
@@ -15,9 +16,35 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bude_internal.h"
 
 using namespace bude;
+
+namespace {
+// Allocations left before the injected failure; 0 = no injection.
+std::atomic<int> g_fail_alloc_in{0};
+}  // namespace
+
+namespace bude {
+
+cudaError_t dev_alloc(void** p, size_t bytes)
+{
+    int k = g_fail_alloc_in.load();
+    while (k > 0 && !g_fail_alloc_in.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+Range::Range(const char* name) { nvtxRangePushA(name); }
+Range::~Range() { nvtxRangePop(); }
+
+}  // namespace bude
 
 struct bude_deck {
     int device = 0;
@@ -314,7 +341,7 @@ int ensure_workspace(double** partial, size_t* pbytes, unsigned** counter, size_
             *pbytes = 0;
         }
         size_t b = std::max(need_bytes, (size_t)1 << 16);
-        CK(cudaMalloc((void**)partial, b), "workspace allocation");
+        CK(dev_alloc((void**)partial, b), "workspace allocation");
         *pbytes = b;
     }
     if (need_count > *ccount) {
@@ -325,7 +352,7 @@ int ensure_workspace(double** partial, size_t* pbytes, unsigned** counter, size_
             *ccount = 0;
         }
         size_t c = std::max(need_count, (size_t)1024);
-        CK(cudaMalloc((void**)counter, c * sizeof(unsigned)), "workspace allocation");
+        CK(dev_alloc((void**)counter, c * sizeof(unsigned)), "workspace allocation");
         CK(cudaMemsetAsync(*counter, 0, c * sizeof(unsigned), s), "workspace clear");
         *ccount = c;
     }
@@ -522,6 +549,15 @@ const char* bude_status_string(int status)
 
 const char* bude_last_error(void) { return g_last_error.c_str(); }
 
+int bude_debug_fail_alloc(int32_t n)
+{
+    if (n < 0) return fail(BUDE_ERR_INVALID_ARG, "bude_debug_fail_alloc: n = %d < 0", n);
+    g_fail_alloc_in.store(n);
+    return BUDE_OK;
+}
+
+int32_t bude_debug_pending_fail_alloc(void) { return g_fail_alloc_in.load(); }
+
 int64_t bude_last_launch_count(void) { return g_launches; }
 
 int bude_get_default_options(int32_t variant, bude_options* out)
@@ -545,6 +581,7 @@ int bude_set_default_options(const bude_options* o)
 
 int bude_create_deck(const bude_deck_desc* desc, void* stream, bude_deck** out)
 {
+    Range range_("bude_create_deck");
     g_launches = 0;
     if (!out) return fail(BUDE_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -578,16 +615,16 @@ int bude_create_deck(const bude_deck_desc* desc, void* stream, bude_deck** out)
     const size_t nl = std::max(1, d->n_lig), np = std::max(1, d->n_pro);
     const size_t pairs = (size_t)std::max(1, d->n_lig < d->n_types ? d->n_lig : d->n_types) *
                          d->n_types;
-    CKD(cudaMalloc((void**)&d->pro, np * sizeof(float4)), "deck allocation");
-    CKD(cudaMalloc((void**)&d->lig, nl * sizeof(float4)), "deck allocation");
-    CKD(cudaMalloc((void**)&d->tabF, pairs * sizeof(PairF)), "deck allocation");
-    CKD(cudaMalloc((void**)&d->tabG, pairs * sizeof(PairG)), "deck allocation");
-    CKD(cudaMalloc((void**)&d->tabD, pairs * sizeof(PairD)), "deck allocation");
-    CKD(cudaMalloc((void**)&d->row_type, (size_t)d->n_types * sizeof(int)), "deck allocation");
-    CKD(cudaMalloc((void**)&d->ff, (size_t)d->n_types * sizeof(float4)), "deck allocation");
+    CKD(dev_alloc((void**)&d->pro, np * sizeof(float4)), "deck allocation");
+    CKD(dev_alloc((void**)&d->lig, nl * sizeof(float4)), "deck allocation");
+    CKD(dev_alloc((void**)&d->tabF, pairs * sizeof(PairF)), "deck allocation");
+    CKD(dev_alloc((void**)&d->tabG, pairs * sizeof(PairG)), "deck allocation");
+    CKD(dev_alloc((void**)&d->tabD, pairs * sizeof(PairD)), "deck allocation");
+    CKD(dev_alloc((void**)&d->row_type, (size_t)d->n_types * sizeof(int)), "deck allocation");
+    CKD(dev_alloc((void**)&d->ff, (size_t)d->n_types * sizeof(float4)), "deck allocation");
     CKD(cudaMemcpyAsync(d->ff, desc->ff, (size_t)d->n_types * sizeof(float4),
                         cudaMemcpyDeviceToDevice, s), "forcefield copy");
-    CKD(cudaMalloc((void**)&tmp, sizeof(Tmp)), "deck allocation");
+    CKD(dev_alloc((void**)&tmp, sizeof(Tmp)), "deck allocation");
     CKD(cudaMemsetAsync(tmp, 0, sizeof(Tmp), s), "memset");
     CKD(launch_pack_protein((const float4*)desc->pro_xyzt, d->pro, d->n_pro, d->n_types,
                             &tmp->err, s),
@@ -618,6 +655,7 @@ int bude_create_deck(const bude_deck_desc* desc, void* stream, bude_deck** out)
 
 int bude_destroy_deck(bude_deck* d)
 {
+    Range range_("bude_destroy_deck");
     if (!d) return BUDE_OK;
     drop_batches_using(d);
     drop_refines_using(d);
@@ -649,12 +687,14 @@ int bude_deck_info(const bude_deck* d, int32_t* n_lig, int32_t* n_pro, int32_t* 
 int bude_energies(bude_deck* deck, const float* poses, int64_t n, float* energies,
                   const bude_options* opts, void* stream)
 {
+    Range range_("bude_energies");
     return run_single(deck, poses, n, energies, nullptr, opts, stream, false);
 }
 
 int bude_pose_grad(bude_deck* deck, const float* poses, int64_t n, float* energies, float* grad,
                    const bude_options* opts, void* stream)
 {
+    Range range_("bude_pose_grad");
     return run_single(deck, poses, n, energies, grad, opts, stream, true);
 }
 
@@ -662,6 +702,7 @@ int bude_energies_batched(bude_deck* const* decks, const float* const* poses, co
                           float* const* energies, int32_t count, const bude_options* opts,
                           void* stream)
 {
+    Range range_("bude_energies_batched");
     g_launches = 0;
     if (count < 0) return fail(BUDE_ERR_INVALID_ARG, "count %d < 0", count);
     if (count == 0) return BUDE_OK;
@@ -708,7 +749,7 @@ int bude_energies_batched(bude_deck* const* decks, const float* const* poses, co
         const Plan& pl = bp->pl;
         auto bail = [&](int code) { delete bp; return code; };
         if (!pl.inst.empty()) {
-            cudaError_t e = cudaMalloc((void**)&bp->dev_table, pl.inst.size() * sizeof(Instance));
+            cudaError_t e = dev_alloc((void**)&bp->dev_table, pl.inst.size() * sizeof(Instance));
             if (e) return bail(cuda_fail(e, "plan allocation"));
             e = cudaMemcpy(bp->dev_table, pl.inst.data(), pl.inst.size() * sizeof(Instance),
                            cudaMemcpyHostToDevice);
@@ -801,6 +842,7 @@ extern "C" BUDE_API int bude_energies_noalloc(bude_deck* deck, const float* pose
                                               float* energies, const bude_options* opts,
                                               void* stream)
 {
+    Range range_("bude_energies_noalloc");
     g_launches = 0;
     if (!deck) return fail(BUDE_ERR_INVALID_ARG, "deck is NULL");
     if (n < 0) return fail(BUDE_ERR_INVALID_ARG, "n = %lld < 0", (long long)n);
@@ -897,6 +939,7 @@ extern "C" BUDE_API int bude_refine(bude_deck* deck, float* poses, int64_t n, in
                                     float step0, float* energies, const bude_options* opts,
                                     void* stream)
 {
+    Range range_("bude_refine");
     g_launches = 0;
     if (!deck) return fail(BUDE_ERR_INVALID_ARG, "deck is NULL");
     if (n < 0 || steps < 0) return fail(BUDE_ERR_INVALID_ARG, "negative n or steps");
@@ -938,7 +981,7 @@ extern "C" BUDE_API int bude_refine(bude_deck* deck, float* poses, int64_t n, in
         rp->deck = deck;
         auto bail = [&](int code) { delete rp; return code; };
         const size_t N = (size_t)n;
-        cudaError_t e = cudaMalloc((void**)&rp->buf, 22 * N * sizeof(float));
+        cudaError_t e = dev_alloc((void**)&rp->buf, 22 * N * sizeof(float));
         if (e) return bail(cuda_fail(e, "refine buffers"));
         float* E = rp->buf;
         float* g = E + N;
@@ -1005,6 +1048,7 @@ extern "C" BUDE_API int bude_param_grad(bude_deck* deck, const float* poses, int
                                         const float* weights, float* lig_grad, float* ff_grad,
                                         const bude_options* opts, void* stream)
 {
+    Range range_("bude_param_grad");
     g_launches = 0;
     if (!deck) return fail(BUDE_ERR_INVALID_ARG, "deck is NULL");
     if (n < 0) return fail(BUDE_ERR_INVALID_ARG, "n = %lld < 0", (long long)n);

@@ -216,6 +216,7 @@ struct bude_hf {
 
 extern "C" BUDE_API int bude_hf_destroy(bude_hf* h)
 {
+    Range range_("bude_hf_destroy");
     if (!h) return BUDE_OK;
     cudaDeviceSynchronize();
     cudaFree(h->geom);
@@ -234,6 +235,7 @@ extern "C" BUDE_API int bude_hf_create(int32_t n_atoms, const double* geom, int3
                                        const double* xpnt, const double* coef, void* stream,
                                        bude_hf** out)
 {
+    Range range_("bude_hf_create");
     if (!out) return BUDE_ERR_INVALID_ARG;
     *out = nullptr;
     if (n_atoms < 1 || ngauss < 1 || ngauss > 8 || !geom || !xpnt || !coef)
@@ -251,14 +253,14 @@ extern "C" BUDE_API int bude_hf_create(int32_t n_atoms, const double* geom, int3
     h->m = (long long)n_atoms * (n_atoms + 1) / 2;
     const size_t e = (size_t)h->m * ngauss * ngauss;
     auto bail = [&](int code) { bude_hf_destroy(h); return code; };
-    if (cudaMalloc((void**)&h->geom, 3 * sizeof(double) * n_atoms) ||
-        cudaMalloc((void**)&h->xc, 2 * sizeof(double) * ngauss) ||
-        cudaMalloc((void**)&h->pq, e * sizeof(double4_32a)) ||
-        cudaMalloc((void**)&h->kp, e * sizeof(double)) ||
-        cudaMalloc((void**)&h->pqf, e * sizeof(float4)) ||
-        cudaMalloc((void**)&h->kpf, e * sizeof(float)) ||
-        cudaMalloc((void**)&h->schwarz, (size_t)h->m * sizeof(double)) ||
-        cudaMalloc((void**)&h->fock, (size_t)n_atoms * n_atoms * sizeof(double)))
+    if (dev_alloc((void**)&h->geom, 3 * sizeof(double) * n_atoms) ||
+        dev_alloc((void**)&h->xc, 2 * sizeof(double) * ngauss) ||
+        dev_alloc((void**)&h->pq, e * sizeof(double4_32a)) ||
+        dev_alloc((void**)&h->kp, e * sizeof(double)) ||
+        dev_alloc((void**)&h->pqf, e * sizeof(float4)) ||
+        dev_alloc((void**)&h->kpf, e * sizeof(float)) ||
+        dev_alloc((void**)&h->schwarz, (size_t)h->m * sizeof(double)) ||
+        dev_alloc((void**)&h->fock, (size_t)n_atoms * n_atoms * sizeof(double)))
         return bail(BUDE_ERR_OOM);
     // host inputs: copied synchronously (plan creation is not on the hot path)
     if (cudaMemcpy(h->geom, geom, 3 * sizeof(double) * n_atoms, cudaMemcpyHostToDevice) ||
@@ -279,6 +281,7 @@ extern "C" BUDE_API int bude_hf_create(int32_t n_atoms, const double* geom, int3
 extern "C" BUDE_API int bude_hf_fock(bude_hf* h, const double* dens, double* g, double tol,
                                      int32_t variant, void* stream)
 {
+    Range range_("bude_hf_fock");
     if (!h || !dens || !g || tol < 0.0 || !std::isfinite(tol)) return BUDE_ERR_INVALID_ARG;
     if (variant != BUDE_FP64 && variant != BUDE_FP32_IEEE) return BUDE_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;

@@ -11,6 +11,21 @@
 
 namespace bude {
 
+// Every device allocation of the library goes through dev_alloc, so that a
+// test can make the n-th one fail (bude_debug_fail_alloc) and check that each
+// error path releases what it took.  An injected failure returns
+// cudaErrorMemoryAllocation without touching the CUDA context.
+cudaError_t dev_alloc(void** p, size_t bytes);
+
+// NVTX range around a public entry point (a no-op unless a profiler is
+// attached).
+struct Range {
+    explicit Range(const char* name);
+    ~Range();
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
+
 // Kernel entry of pose_kernel<V, P, G>, or nullptr when that combination is
 // not built.  Defined in the per-variant translation units.
 const void* kernel_ieee(int P, bool G);

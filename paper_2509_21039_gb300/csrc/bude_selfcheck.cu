@@ -26,11 +26,12 @@ __global__ void sqrt_selfcheck_kernel(unsigned long long lo, unsigned long long 
 extern "C" BUDE_API int bude_selfcheck_sqrt(uint64_t* mismatches, uint32_t* first_bad,
                                             void* stream)
 {
+    bude::Range range_("bude_selfcheck_sqrt");
     if (!mismatches) return BUDE_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     struct R { unsigned long long n; unsigned first; unsigned pad; };
     R* d = nullptr;
-    if (cudaMalloc((void**)&d, sizeof(R)) != cudaSuccess) return BUDE_ERR_OOM;
+    if (bude::dev_alloc((void**)&d, sizeof(R)) != cudaSuccess) return BUDE_ERR_OOM;
     R h{0ull, 0xffffffffu, 0u};
     cudaError_t e = cudaMemcpyAsync(d, &h, sizeof h, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {

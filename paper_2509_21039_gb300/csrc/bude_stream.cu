@@ -234,6 +234,7 @@ cudaError_t laplacian_launch(const T* u, T* f, int nx, int ny, int nz, T cx, T c
 extern "C" BUDE_API int bude_stream(int32_t op, int32_t dtype, void* a, void* b, void* c,
                                     double scalar, int64_t n, double* dot_result, void* stream)
 {
+    Range range_("bude_stream");
     if (op < 0 || op > 4 || (dtype != 0 && dtype != 1) || n < 0) return BUDE_ERR_INVALID_ARG;
     if (n == 0) {
         if (op == kDot && dot_result)
@@ -262,6 +263,7 @@ extern "C" BUDE_API int bude_laplacian(int32_t dtype, const void* u, void* f, in
                                        int32_t ny, int32_t nz, double invhx2, double invhy2,
                                        double invhz2, double invhxyz2, void* stream)
 {
+    Range range_("bude_laplacian");
     if ((dtype != 0 && dtype != 1) || nx < 0 || ny < 0 || nz < 0) return BUDE_ERR_INVALID_ARG;
     if (nx < 3 || ny < 3 || nz < 3) return BUDE_OK;  // no interior points
     if (!u || !f || u == f) return BUDE_ERR_INVALID_ARG;
