@@ -89,7 +89,22 @@ typedef struct {
     int32_t block;       /* threads per CTA: multiple of 32 in [64, 1024] */
     int32_t tile;        /* protein atoms staged per shared-memory chunk */
     int32_t ctas_per_sm; /* resident CTAs per SM of the persistent grid */
+    int32_t cull;        /* 1: cutoff culling in the energy kernels (below); 0: default */
 } bude_options;
+
+/*
+ * Cutoff culling (bude_options.cull = 1; no paper counterpart, off by
+ * default).  Every term of the pair energy is exactly zero once d reaches
+ * R + max(D_E, D_D) = R + 4 A.  With culling on, a warp computes the squared
+ * distances of all its poses to a protein atom first and, when every one of
+ * them lies beyond that cutoff (with a margin for the roots' rounding), skips
+ * the roots and the terms for that atom.  The skipped terms would have added
+ * exact zeros, so the energies are bit-identical to the unculled kernel of
+ * the same launch shape.  Built for the FP32 energy kernels with an even
+ * ppwi (bude_energies, bude_energies_batched, bude_energies_noalloc); other
+ * calls and shapes ignore the flag.  Culled launches evaluate fewer pairs
+ * than Eq. 3 counts, so their FLOP rate is not comparable with Eq. 3.
+ */
 
 typedef struct bude_deck bude_deck;
 typedef struct bude_batch bude_batch;

@@ -50,7 +50,7 @@ class DeckDesc(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("ppwi", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("cull", ctypes.c_int32)]
 
 
 _lib = None
@@ -157,10 +157,11 @@ class LaunchOptions:
     block: int = 0
     tile: int = 0
     ctas_per_sm: int = 0
+    cull: int = 0
 
     def c(self) -> Options:
         v = VARIANTS[self.variant] if isinstance(self.variant, str) else self.variant
-        return Options(v, self.ppwi, self.block, self.tile, self.ctas_per_sm)
+        return Options(v, self.ppwi, self.block, self.tile, self.ctas_per_sm, self.cull)
 
 
 def _opts(opts=None, **kw) -> Options:
@@ -175,7 +176,7 @@ def default_options(variant) -> LaunchOptions:
     v = VARIANTS[variant] if isinstance(variant, str) else variant
     o = Options()
     _check(load().bude_get_default_options(v, ctypes.byref(o)))
-    return LaunchOptions(o.variant, o.ppwi, o.block, o.tile, o.ctas_per_sm)
+    return LaunchOptions(o.variant, o.ppwi, o.block, o.tile, o.ctas_per_sm, o.cull)
 
 
 def set_default_options(opts: LaunchOptions):

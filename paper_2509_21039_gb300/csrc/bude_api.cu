@@ -70,10 +70,10 @@ thread_local int64_t g_launches = 0;
 
 std::mutex g_opt_mutex;
 bude_options g_default[4] = {
-    {BUDE_FP32_IEEE, 8, 256, 0, 1},
-    {BUDE_FP32_FAST, 8, 256, 0, 1},
-    {BUDE_FP32_COMP, 8, 256, 0, 1},
-    {BUDE_FP64, 2, 256, 0, 1},
+    {BUDE_FP32_IEEE, 8, 256, 0, 1, 0},
+    {BUDE_FP32_FAST, 8, 256, 0, 1, 0},
+    {BUDE_FP32_COMP, 8, 256, 0, 1, 0},
+    {BUDE_FP64, 2, 256, 0, 1, 0},
 };
 
 int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
@@ -128,8 +128,17 @@ DeviceInfo device_info(int dev)
     return d;
 }
 
-const void* kernel_for(int variant, int P, bool G)
+const void* kernel_for(int variant, int P, bool G, bool cull = false)
 {
+    // cutoff culling is built for the packed FP32 energy kernels; elsewhere
+    // the flag is ignored (the results are the same either way)
+    if (cull && !G && P % 2 == 0) {
+        switch (variant) {
+        case BUDE_FP32_IEEE: return kernel_ieee_cull(P);
+        case BUDE_FP32_FAST: return kernel_fast_cull(P);
+        case BUDE_FP32_COMP: return kernel_comp_cull(P);
+        }
+    }
     switch (variant) {
     case BUDE_FP32_IEEE: return kernel_ieee(P, G);
     case BUDE_FP32_FAST: return kernel_fast(P, G);
@@ -181,7 +190,7 @@ size_t smem_fixed(int variant, int P, bool G, int block)
 constexpr size_t kStaticSmem = 256;
 
 struct Resolved {
-    int variant, P, block, tile, cps;
+    int variant, P, block, tile, cps, cull;
 };
 
 int resolve_options(const bude_options* o, bool G, Resolved* r)
@@ -198,6 +207,8 @@ int resolve_options(const bude_options* o, bool G, Resolved* r)
     r->block = (o && o->block) ? o->block : d.block;
     r->tile = (o && o->tile) ? o->tile : d.tile;
     r->cps = (o && o->ctas_per_sm) ? o->ctas_per_sm : d.ctas_per_sm;
+    r->cull = (o && o->cull) ? o->cull : d.cull;
+    if (r->cull != 0 && r->cull != 1) return fail(BUDE_ERR_INVALID_ARG, "cull %d: need 0 or 1", r->cull);
     if (G && variant != BUDE_FP64 && r->P > 8) r->P = 8;
     if (G && variant == BUDE_FP64 && r->P > 4) r->P = 4;
     if (r->block < 64 || r->block > 1024 || r->block % 32)
@@ -303,7 +314,7 @@ int make_plan(const std::vector<const bude_deck*>& decks, const std::vector<cons
     pl->n_total = k;
     pl->n_tiles = tiles;
     pl->smem = smem_max;
-    pl->fn = kernel_for(r.variant, r.P, G);
+    pl->fn = kernel_for(r.variant, r.P, G, r.cull != 0);
     if (pl->inst.empty()) return BUDE_OK;
     CK(cudaFuncSetAttribute(pl->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem),
        "cudaFuncSetAttribute");
@@ -575,7 +586,7 @@ int bude_set_default_options(const bude_options* o)
     int rc = resolve_options(o, false, &r);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(g_opt_mutex);
-    g_default[o->variant] = {r.variant, r.P, r.block, r.tile, r.cps};
+    g_default[o->variant] = {r.variant, r.P, r.block, r.tile, r.cps, r.cull};
     return BUDE_OK;
 }
 

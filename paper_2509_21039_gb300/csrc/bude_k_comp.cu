@@ -12,6 +12,21 @@ template __global__ void pose_kernel<kCOMP, 1, true>(const Args);
 template __global__ void pose_kernel<kCOMP, 2, true>(const Args);
 template __global__ void pose_kernel<kCOMP, 4, true>(const Args);
 template __global__ void pose_kernel<kCOMP, 8, true>(const Args);
+template __global__ void pose_kernel<kCOMP, 2, false, true>(const Args);
+template __global__ void pose_kernel<kCOMP, 4, false, true>(const Args);
+template __global__ void pose_kernel<kCOMP, 8, false, true>(const Args);
+template __global__ void pose_kernel<kCOMP, 16, false, true>(const Args);
+
+const void* kernel_comp_cull(int P)
+{
+    switch (P) {
+    case 2: return (const void*)pose_kernel<kCOMP, 2, false, true>;
+    case 4: return (const void*)pose_kernel<kCOMP, 4, false, true>;
+    case 8: return (const void*)pose_kernel<kCOMP, 8, false, true>;
+    case 16: return (const void*)pose_kernel<kCOMP, 16, false, true>;
+    }
+    return nullptr;
+}
 
 const void* kernel_comp(int P, bool G)
 {

@@ -12,6 +12,21 @@ template __global__ void pose_kernel<kFAST, 1, true>(const Args);
 template __global__ void pose_kernel<kFAST, 2, true>(const Args);
 template __global__ void pose_kernel<kFAST, 4, true>(const Args);
 template __global__ void pose_kernel<kFAST, 8, true>(const Args);
+template __global__ void pose_kernel<kFAST, 2, false, true>(const Args);
+template __global__ void pose_kernel<kFAST, 4, false, true>(const Args);
+template __global__ void pose_kernel<kFAST, 8, false, true>(const Args);
+template __global__ void pose_kernel<kFAST, 16, false, true>(const Args);
+
+const void* kernel_fast_cull(int P)
+{
+    switch (P) {
+    case 2: return (const void*)pose_kernel<kFAST, 2, false, true>;
+    case 4: return (const void*)pose_kernel<kFAST, 4, false, true>;
+    case 8: return (const void*)pose_kernel<kFAST, 8, false, true>;
+    case 16: return (const void*)pose_kernel<kFAST, 16, false, true>;
+    }
+    return nullptr;
+}
 
 const void* kernel_fast(int P, bool G)
 {

@@ -75,23 +75,26 @@ def time_call(fn, reps: int = 5, warmup: int = 1) -> float:
     return statistics.median(ms)
 
 
-def candidates(variant: str, space=None, grad: bool = False):
+def candidates(variant: str, space=None, grad: bool = False, cull: int = 0):
     sp = dict(SPACE if space is None else space)
     ps = sp["ppwi"]
     if variant == "fp64":
         ps = [p for p in ps if p <= 4]
     if grad:
         ps = [p for p in ps if p <= 8]
+    if cull:
+        ps = [p for p in ps if p % 2 == 0]   # culling is built for even P
     for p, b, c, t in itertools.product(ps, sp["block"], sp["ctas_per_sm"], sp["tile"]):
-        yield bude.LaunchOptions(variant=variant, ppwi=p, block=b, ctas_per_sm=c, tile=t)
+        yield bude.LaunchOptions(variant=variant, ppwi=p, block=b, ctas_per_sm=c, tile=t,
+                                 cull=cull)
 
 
 def tune_plain(deck, poses, variant: str, space=None, reps: int = 5, grad: bool = False,
-               log=None):
+               log=None, cull: int = 0):
     """Fastest launch shape of bude_energies (or bude_pose_grad) on this input."""
     out = torch.empty(poses.shape[1], dtype=torch.float32, device=poses.device)
     results = []
-    for o in candidates(variant, space, grad):
+    for o in candidates(variant, space, grad, cull):
         if grad:
             fn = lambda: bude.pose_grad(deck, poses, want_energy=True, opts=o)  # noqa: E731
         else:
@@ -105,7 +108,7 @@ def tune_plain(deck, poses, variant: str, space=None, reps: int = 5, grad: bool 
         results.append((ms, o))
         if log:
             log(f"{variant} P={o.ppwi:2d} block={o.block:4d} cps={o.ctas_per_sm} "
-                f"tile={o.tile}: {ms:.3f} ms")
+                f"tile={o.tile} cull={o.cull}: {ms:.3f} ms")
     results.sort(key=lambda r: r[0])
     return results
 
@@ -131,6 +134,8 @@ def tune_batched(decks, poses, variant: str, space=None, reps: int = 5, log=None
 def record(table: dict, k: str, ms: float, o) -> None:
     table[k] = {"ppwi": o.ppwi, "block": o.block, "ctas_per_sm": o.ctas_per_sm,
                 "tile": o.tile, "ms": round(ms, 4)}
+    if o.cull:
+        table[k]["cull"] = o.cull
 
 
 def lookup(variant: str, n_lig: int, n_pro: int, n_poses: int, mode: str = "plain",
@@ -141,7 +146,8 @@ def lookup(variant: str, n_lig: int, n_pro: int, n_poses: int, mode: str = "plai
     if e is None:
         return None
     return bude.LaunchOptions(variant=variant, ppwi=e["ppwi"], block=e["block"],
-                              ctas_per_sm=e["ctas_per_sm"], tile=e["tile"])
+                              ctas_per_sm=e["ctas_per_sm"], tile=e["tile"],
+                              cull=e.get("cull", 0))
 
 
 def apply(variants=("ieee", "fast", "comp", "fp64"), n_lig=64, n_pro=2672, n_poses=65536):
@@ -159,6 +165,8 @@ def _workloads(which):
         yield "small", [synth.make_deck(0, **synth.SMALL)]
     if "full" in which:
         yield "full", [synth.make_deck(1, **synth.FULL)]
+    if "cull" in which:
+        yield "cull", [synth.make_deck(1, **synth.FULL)]
     if "grad" in which:
         yield "grad", [synth.make_deck(4, **synth.GRAD)]
     if "batched" in which:
@@ -200,6 +208,13 @@ def main(argv=None):
                 res = tune_batched(decks, poses, v, space, a.reps, log)
                 b = "x".join(str(len(decks_np)) for _ in [0])
                 k = key(v, f"n{b}", "batched")
+            elif name == "cull":
+                if v == "fp64":
+                    continue
+                d = decks_np[0]
+                res = tune_plain(decks[0], poses[0], v, space, a.reps, log=log, cull=1)
+                k = key(v, bucket(len(d["lig_type"]), len(d["pro_type"]), d["poses"].shape[1]),
+                        "cull")
             elif name == "grad":
                 if v not in ("fast", "ieee"):
                     continue
