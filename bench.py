@@ -222,6 +222,12 @@ def batched_vs_plain(bude, synth, tune, dev, timed, variant="fast", count=64, se
 
     ms_b, lb = timed(run_batched, 10, 3)
     ms_p, lp = timed(run_plain, 10, 3)
+    # the same batched launch with cutoff culling (opt-in; bit-identical)
+    ob_c = bude.LaunchOptions(variant=ob.variant, ppwi=ob.ppwi, block=ob.block,
+                              ctas_per_sm=ob.ctas_per_sm, tile=ob.tile, cull=1)
+    outs_c = [torch.empty_like(o) for o in outs_b]
+    ms_c, _ = timed(lambda: bude.energies_batched(decks, poses, outs_c, opts=ob_c), 10, 3)
+    cull_same = all(bool(torch.equal(a, c)) for a, c in zip(outs_b, outs_c))
     pairs = sum(len(d["lig_type"]) * len(d["pro_type"]) * d["poses"].shape[1] for d in decks_np)
     n = sum(d["poses"].shape[1] for d in decks_np)
     diff = max(float(((a - b).abs() / b.abs().clamp_min(1.0)).max()) for a, b in zip(outs_b, outs_p))
@@ -234,7 +240,8 @@ def batched_vs_plain(bude, synth, tune, dev, timed, variant="fast", count=64, se
             "batched_poses_per_s": n / (tb / 1e3), "plain_poses_per_s": n / (tp / 1e3),
             "batched_launches": lb // 10, "plain_launches": plain_launches[0],
             "batched_opts": {"ppwi": ob.ppwi, "block": ob.block, "ctas_per_sm": ob.ctas_per_sm},
-            "max_rel_diff_batched_vs_plain": diff}
+            "max_rel_diff_batched_vs_plain": diff,
+            "batched_cull_ms": statistics.mean(ms_c), "batched_cull_bit_identical": cull_same}
 
 
 def adjoint_throughput(bude, synth, tune, dev, timed, variant="fast"):
@@ -246,11 +253,24 @@ def adjoint_throughput(bude, synth, tune, dev, timed, variant="fast"):
     o = tune.lookup(variant, 64, 2672, D["poses"].shape[1], mode="grad") or \
         bude.LaunchOptions(variant=variant)
     ms, _ = timed(lambda: bude.pose_grad(deck, P, opts=o), 10, 3)
+    oc = tune.lookup(variant, 64, 2672, D["poses"].shape[1], mode="grad_cull") or \
+        bude.LaunchOptions(variant=variant, ppwi=o.ppwi, block=o.block,
+                           ctas_per_sm=o.ctas_per_sm, tile=o.tile)
+    oc.cull = 1
+    ms_c, _ = timed(lambda: bude.pose_grad(deck, P, opts=oc), 10, 3)
+    # bit-identity against the unculled kernel of the culled launch's shape
+    e1, g1 = bude.pose_grad(deck, P, opts=oc)
+    ou = bude.LaunchOptions(variant=oc.variant, ppwi=oc.ppwi, block=oc.block,
+                            ctas_per_sm=oc.ctas_per_sm, tile=oc.tile, cull=0)
+    e2, g2 = bude.pose_grad(deck, P, opts=ou)
+    same = bool(torch.equal(e1, e2) and torch.equal(g1, g2))
     deck.close()
     t = statistics.mean(ms)
     return {"workload": "64 lig x 2672 pro x 16384 poses, seed 4", "variant": variant,
             "ms": t, "poses_per_s": P.shape[1] / (t / 1e3),
-            "opts": {"ppwi": o.ppwi, "block": o.block, "ctas_per_sm": o.ctas_per_sm}}
+            "opts": {"ppwi": o.ppwi, "block": o.block, "ctas_per_sm": o.ctas_per_sm},
+            "cull_ms": statistics.mean(ms_c), "cull_bit_identical": same,
+            "cull_opts": {"ppwi": oc.ppwi, "block": oc.block, "ctas_per_sm": oc.ctas_per_sm}}
 
 
 def refine_throughput(bude, synth, tune, dev, timed, variant="fast", steps=10):
@@ -270,12 +290,23 @@ def refine_throughput(bude, synth, tune, dev, timed, variant="fast", steps=10):
         bude.refine_device(deck, P, steps=steps, step0=0.05, energies=E, opts=o)
 
     ms, launches = timed(step, 5, 2)
+    Pa, Ea = P.clone(), E.clone()
+    oc = bude.LaunchOptions(variant=o.variant, ppwi=o.ppwi, block=o.block,
+                            ctas_per_sm=o.ctas_per_sm, tile=o.tile, cull=1)
+
+    def step_c():
+        P.copy_(P0)
+        bude.refine_device(deck, P, steps=steps, step0=0.05, energies=E, opts=oc)
+
+    ms_c, _ = timed(step_c, 5, 2)
+    same = bool(torch.equal(Pa, P) and torch.equal(Ea, E))
     deck.close()
     t = statistics.mean(ms)
     return {"workload": f"{steps} steps x 16384 poses, 64 lig x 2672 pro, seed 4",
             "variant": variant, "ms": t, "pose_steps_per_s": steps * P.shape[1] / (t / 1e3),
             "graph_launches_per_call": 1, "kernels_per_call": launches // 5,
-            "mean_energy_before": e0, "mean_energy_after": E.mean().item()}
+            "mean_energy_before": e0, "mean_energy_after": Ea.mean().item(),
+            "cull_ms": statistics.mean(ms_c), "cull_bit_identical": same}
 
 
 def cull_throughput(bude, tune, deck, poses, out, ms_brute, timed, variant="fast"):

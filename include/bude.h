@@ -100,10 +100,12 @@ typedef struct {
  * them lies beyond that cutoff (with a margin for the roots' rounding), skips
  * the roots and the terms for that atom.  The skipped terms would have added
  * exact zeros, so the energies are bit-identical to the unculled kernel of
- * the same launch shape.  Built for the FP32 energy kernels with an even
- * ppwi (bude_energies, bude_energies_batched, bude_energies_noalloc); other
- * calls and shapes ignore the flag.  Culled launches evaluate fewer pairs
- * than Eq. 3 counts, so their FLOP rate is not comparable with Eq. 3.
+ * the same launch shape; so are the pose gradients, whose terms and
+ * derivatives vanish there too.  Built for the FP32 kernels with an even ppwi
+ * (bude_energies, bude_energies_batched, bude_energies_noalloc,
+ * bude_pose_grad, bude_refine); FP64, odd ppwi and bude_param_grad ignore the
+ * flag.  Culled launches evaluate fewer pairs than Eq. 3 counts, so their
+ * FLOP rate is not comparable with Eq. 3.
  */
 
 typedef struct bude_deck bude_deck;

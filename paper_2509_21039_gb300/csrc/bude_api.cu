@@ -130,13 +130,13 @@ DeviceInfo device_info(int dev)
 
 const void* kernel_for(int variant, int P, bool G, bool cull = false)
 {
-    // cutoff culling is built for the packed FP32 energy kernels; elsewhere
+    // cutoff culling is built for the packed FP32 kernels (even P); elsewhere
     // the flag is ignored (the results are the same either way)
-    if (cull && !G && P % 2 == 0) {
+    if (cull && P % 2 == 0) {
         switch (variant) {
-        case BUDE_FP32_IEEE: return kernel_ieee_cull(P);
-        case BUDE_FP32_FAST: return kernel_fast_cull(P);
-        case BUDE_FP32_COMP: return kernel_comp_cull(P);
+        case BUDE_FP32_IEEE: return kernel_ieee_cull(P, G);
+        case BUDE_FP32_FAST: return kernel_fast_cull(P, G);
+        case BUDE_FP32_COMP: return kernel_comp_cull(P, G);
         }
     }
     switch (variant) {

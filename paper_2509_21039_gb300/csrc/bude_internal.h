@@ -32,10 +32,10 @@ const void* kernel_ieee(int P, bool G);
 const void* kernel_fast(int P, bool G);
 const void* kernel_comp(int P, bool G);
 const void* kernel_f64(int P, bool G);
-// pose_kernel<V, P, false, true>: energies with cutoff culling (even P only).
-const void* kernel_ieee_cull(int P);
-const void* kernel_fast_cull(int P);
-const void* kernel_comp_cull(int P);
+// pose_kernel<V, P, G, true>: energies or adjoint with cutoff culling (even P).
+const void* kernel_ieee_cull(int P, bool G);
+const void* kernel_fast_cull(int P, bool G);
+const void* kernel_comp_cull(int P, bool G);
 
 cudaError_t launch_pack_protein(const float4* src, float4* dst, int n, int n_types,
                                 unsigned* err, cudaStream_t s);

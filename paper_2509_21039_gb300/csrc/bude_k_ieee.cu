@@ -16,14 +16,25 @@ template __global__ void pose_kernel<kIEEE, 2, false, true>(const Args);
 template __global__ void pose_kernel<kIEEE, 4, false, true>(const Args);
 template __global__ void pose_kernel<kIEEE, 8, false, true>(const Args);
 template __global__ void pose_kernel<kIEEE, 16, false, true>(const Args);
+template __global__ void pose_kernel<kIEEE, 2, true, true>(const Args);
+template __global__ void pose_kernel<kIEEE, 4, true, true>(const Args);
+template __global__ void pose_kernel<kIEEE, 8, true, true>(const Args);
 
-const void* kernel_ieee_cull(int P)
+const void* kernel_ieee_cull(int P, bool G)
 {
-    switch (P) {
-    case 2: return (const void*)pose_kernel<kIEEE, 2, false, true>;
-    case 4: return (const void*)pose_kernel<kIEEE, 4, false, true>;
-    case 8: return (const void*)pose_kernel<kIEEE, 8, false, true>;
-    case 16: return (const void*)pose_kernel<kIEEE, 16, false, true>;
+    if (!G) {
+        switch (P) {
+        case 2: return (const void*)pose_kernel<kIEEE, 2, false, true>;
+        case 4: return (const void*)pose_kernel<kIEEE, 4, false, true>;
+        case 8: return (const void*)pose_kernel<kIEEE, 8, false, true>;
+        case 16: return (const void*)pose_kernel<kIEEE, 16, false, true>;
+        }
+    } else {
+        switch (P) {
+        case 2: return (const void*)pose_kernel<kIEEE, 2, true, true>;
+        case 4: return (const void*)pose_kernel<kIEEE, 4, true, true>;
+        case 8: return (const void*)pose_kernel<kIEEE, 8, true, true>;
+        }
     }
     return nullptr;
 }

@@ -169,6 +169,8 @@ def _workloads(which):
         yield "cull", [synth.make_deck(1, **synth.FULL)]
     if "grad" in which:
         yield "grad", [synth.make_deck(4, **synth.GRAD)]
+    if "grad_cull" in which:
+        yield "grad_cull", [synth.make_deck(4, **synth.GRAD)]
     if "batched" in which:
         yield "batched", synth.make_batched(3, 64)
 
@@ -215,13 +217,14 @@ def main(argv=None):
                 res = tune_plain(decks[0], poses[0], v, space, a.reps, log=log, cull=1)
                 k = key(v, bucket(len(d["lig_type"]), len(d["pro_type"]), d["poses"].shape[1]),
                         "cull")
-            elif name == "grad":
+            elif name in ("grad", "grad_cull"):
                 if v not in ("fast", "ieee"):
                     continue
                 d = decks_np[0]
-                res = tune_plain(decks[0], poses[0], v, space, a.reps, grad=True, log=log)
+                res = tune_plain(decks[0], poses[0], v, space, a.reps, grad=True, log=log,
+                                 cull=int(name == "grad_cull"))
                 k = key(v, bucket(len(d["lig_type"]), len(d["pro_type"]), d["poses"].shape[1]),
-                        "grad")
+                        name)
             else:
                 d = decks_np[0]
                 res = tune_plain(decks[0], poses[0], v, space, a.reps, log=log)

@@ -1,8 +1,9 @@
 """Cutoff culling (bude_options.cull): a warp skips a protein atom when every
-one of its poses is beyond the pair's cutoff R + 4 A, where every term is
-exactly zero.  The energies must be bit-identical to the unculled kernel of
-the same launch shape, for every packed FP32 variant and shape, and on decks
-where nothing, some or everything is culled.
+one of its poses is beyond the pair's cutoff R + 4 A, where every term (and
+its derivative) is exactly zero.  Energies, pose gradients and refinement
+must be bit-identical to the unculled kernels of the same launch shape, for
+every packed FP32 variant and shape, and on decks where nothing, some or
+everything is culled.
 """
 import numpy as np
 import pytest
@@ -96,6 +97,33 @@ def test_negative_hardness_and_batched_and_noalloc():
         d.close()
 
 
+@pytest.mark.parametrize("variant,ppwi,block", [("ieee", 4, 384), ("fast", 4, 384), ("comp", 2, 256),
+                                                ("fast", 8, 128), ("ieee", 2, 512)])
+def test_culled_pose_gradients_are_bit_identical(variant, ppwi, block):
+    D = synth.make_deck(157, 16, 800, 34, 1500)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    e0, g0 = bude.pose_grad(deck, P, opts=bude.LaunchOptions(variant=variant, ppwi=ppwi, block=block))
+    e1, g1 = bude.pose_grad(deck, P, opts=bude.LaunchOptions(variant=variant, ppwi=ppwi, block=block,
+                                                                cull=1))
+    torch.cuda.synchronize()
+    assert torch.equal(e0, e1) and torch.equal(g0, g1)
+    deck.close()
+
+
+def test_culled_refinement_is_bit_identical():
+    D = synth.make_deck(158, 12, 600, 34, 700)
+    deck = bude.Deck(D, device=DEV)
+    P0 = torch.from_numpy(D["poses"]).to(DEV)
+    A, B = P0.clone(), P0.clone()
+    ea = bude.refine_device(deck, A, steps=5, opts=bude.LaunchOptions(variant="fast", ppwi=4, block=384))
+    eb = bude.refine_device(deck, B, steps=5, opts=bude.LaunchOptions(variant="fast", ppwi=4, block=384,
+                                                                      cull=1))
+    torch.cuda.synchronize()
+    assert torch.equal(ea, eb) and torch.equal(A, B)
+    deck.close()
+
+
 def test_cull_flag_is_checked_and_ignored_where_not_built():
     D = synth.make_deck(156, 6, 200, 34, 300)
     deck = bude.Deck(D, device=DEV)
@@ -103,7 +131,7 @@ def test_cull_flag_is_checked_and_ignored_where_not_built():
     with pytest.raises(bude.BudeError) as e:
         bude.energies(deck, P, opts=bude.LaunchOptions(variant="fast", cull=2))
     assert e.value.code == bude.ERR_INVALID_ARG
-    # odd ppwi, FP64 and the adjoint ignore the flag
+    # odd ppwi and FP64 ignore the flag
     for kw in (dict(variant="ieee", ppwi=1), dict(variant="fp64", ppwi=2)):
         a = bude.energies(deck, P, opts=bude.LaunchOptions(cull=0, **kw)).cpu().numpy()
         b = bude.energies(deck, P, opts=bude.LaunchOptions(cull=1, **kw)).cpu().numpy()
