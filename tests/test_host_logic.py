@@ -1,0 +1,166 @@
+"""Host-side logic that needs no GPU: the Eq. 3 FLOP count and the roofline
+bookkeeping of bench.py, the autotuner's table and search space, the seeded
+input generators and the options struct of the binding."""
+import ctypes
+import importlib.util
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2509_21039_gb300 import bude, synth, tune
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_eq3_counts_one_work_item_by_hand(bench):
+    # Eq. 3 for one work-item of P poses: 28 P + nlig (2 + 18 P + npro (10 + 30 P))
+    # 2 ligand atoms, 3 protein atoms, P = 4: 112 + 2 (2 + 72 + 3 * 130) = 1040 per item,
+    # and 8 poses are two items
+    assert bench.eq3_flops(2, 3, 8, 4) == 2080
+    # P = 1: 28 + 2 (2 + 18 + 3 * 40) = 308 per pose
+    assert bench.eq3_flops(2, 3, 5, 1) == 5 * 308
+
+
+def test_eq3_many_pose_limit_is_the_algorithmic_count(bench):
+    # the per-pose Eq. 3 count falls towards 28 + nlig (18 + 30 npro) as P grows;
+    # the pose-independent 2 + 10 npro per ligand atom is spread over P poses
+    n_lig, n_pro, n = 64, 2672, 65536
+    alg = bench.algorithmic_flops(n_lig, n_pro, n)
+    assert alg == n * (28 + n_lig * (18 + 30 * n_pro))
+    prev = None
+    for p in (1, 2, 4, 8, 16, 1024):
+        e = bench.eq3_flops(n_lig, n_pro, n, p)
+        assert e > alg
+        assert prev is None or e < prev
+        assert e - alg == pytest.approx(n * n_lig * (2 + 10 * n_pro) / p)
+        prev = e
+    # the full-size config: 3.363e11 FLOP per launch
+    assert alg == pytest.approx(3.363e11, rel=1e-3)
+
+
+def test_measured_constants_are_gated_by_source_and_shape(bench):
+    m = bench.MEASURED_TRAFFIC
+    sha = bench.kernel_sha()
+    assert len(sha) == 16
+    hit = bench.measured_traffic(m["variant"], m["ppwi"], m["block"], bench.FULL["n_poses"])
+    assert hit == (m["bytes"] if sha == m["kernel_sha256_16"] else None)
+    # any other shape or workload is never reported
+    assert bench.measured_traffic(m["variant"], m["ppwi"] * 2, m["block"], bench.FULL["n_poses"]) is None
+    assert bench.measured_traffic(m["variant"], m["ppwi"], m["block"], 4096) is None
+    assert bench.measured_traffic("ieee", m["ppwi"], m["block"], bench.FULL["n_poses"]) is None
+    x = bench.measured_executed("fast")
+    assert x is None or 10.0 < x <= 30.0
+
+
+def test_tuner_buckets_and_keys():
+    assert tune.bucket(64, 2672, 65536) == "p16_k18"
+    assert tune.bucket(26, 938, 4096) == "p12_k15"
+    assert tune.bucket(0, 0, 0) == "p0_k0"
+    b = tune.bucket(64, 2672, 16384)
+    assert b == "p14_k18"
+
+
+def test_tuner_search_space_respects_what_is_built():
+    ps = {o.ppwi for o in tune.candidates("fp64")}
+    assert ps == {1, 2, 4}
+    ps = {o.ppwi for o in tune.candidates("ieee", grad=True)}
+    assert ps == {1, 2, 4, 8}
+    cs = list(tune.candidates("fast", cull=1))
+    assert {o.ppwi for o in cs} == {2, 4, 8, 16} and all(o.cull == 1 for o in cs)
+    n = len(list(tune.candidates("fast")))
+    assert n == 5 * 7 * 4
+
+
+def test_tuned_table_record_and_lookup_roundtrip(tmp_path, monkeypatch):
+    monkeypatch.setattr(tune, "gpu_name", lambda: "TEST_GPU")
+    t = {}
+    o = bude.LaunchOptions(variant="fast", ppwi=16, block=384, ctas_per_sm=2, tile=0, cull=1)
+    tune.record(t, tune.key("fast", "p16_k18", "cull"), 2.5, o)
+    tune.record(t, tune.key("fast", "p16_k18"), 4.8,
+                bude.LaunchOptions(variant="fast", ppwi=8, block=512, ctas_per_sm=1))
+    path = str(tmp_path / "t.json")
+    tune.save_table(t, path)
+    t2 = tune.load_table(path)
+    assert t2 == t
+    got = tune.lookup("fast", 64, 2672, 65536, mode="cull", table=t2)
+    assert (got.ppwi, got.block, got.ctas_per_sm, got.cull) == (16, 384, 2, 1)
+    got = tune.lookup("fast", 64, 2672, 65536, table=t2)
+    assert (got.ppwi, got.block, got.cull) == (8, 512, 0)
+    assert tune.lookup("ieee", 64, 2672, 65536, table=t2) is None
+    assert tune.load_table(str(tmp_path / "missing.json")) == {}
+
+
+def test_committed_tuned_table_is_well_formed():
+    t = tune.load_table()
+    assert t, "tuned.json is committed"
+    for k, e in t.items():
+        gpu, variant, mode, b = k.split("|")
+        assert variant in ("fast", "ieee", "comp", "fp64")
+        assert mode in ("plain", "grad", "batched", "cull", "grad_cull")
+        assert e["ppwi"] in (1, 2, 4, 8, 16)
+        assert 64 <= e["block"] <= 1024 and e["block"] % 32 == 0
+        assert 1 <= e["ctas_per_sm"] <= 4 and e["ms"] > 0
+        if mode.startswith("grad"):
+            assert e["ppwi"] <= 8
+        if e.get("cull"):
+            assert e["ppwi"] % 2 == 0
+    full = [k for k in t if k.endswith("|fast|plain|p16_k18")]
+    assert full, "the headline workload has a tuned FAST shape"
+
+
+def test_options_struct_matches_the_header():
+    # six int32 fields in the order of include/bude.h
+    assert ctypes.sizeof(bude.Options) == 6 * 4
+    names = [f[0] for f in bude.Options._fields_]
+    assert names == ["variant", "ppwi", "block", "tile", "ctas_per_sm", "cull"]
+    text = open(os.path.join(ROOT, "include", "bude.h")).read()
+    body = text[text.index("typedef struct {\n    int32_t variant;"):]
+    body = body[:body.index("} bude_options;")]
+    assert [line.split()[1].rstrip(";") for line in body.splitlines()[1:]] == names
+
+
+def test_synthetic_decks_are_seeded_and_in_range():
+    a = synth.make_deck(3, 20, 100, 34, 50)
+    b = synth.make_deck(3, 20, 100, 34, 50)
+    c = synth.make_deck(4, 20, 100, 34, 50)
+    for k in synth.DECK_KEYS + ("poses",):
+        np.testing.assert_array_equal(a[k], b[k])
+    assert not np.array_equal(a["pro_xyz"], c["pro_xyz"])
+    assert a["pro_xyz"].shape == (100, 3) and a["lig_xyz"].shape == (20, 3)
+    assert a["poses"].shape == (6, 50) and a["poses"].dtype == np.float32
+    assert np.all(np.abs(a["pro_xyz"]) <= 20) and np.all(np.abs(a["lig_xyz"]) <= 4)
+    assert a["pro_type"].min() >= 0 and a["pro_type"].max() < 34
+    assert np.all((a["radius"] >= 1.4) & (a["radius"] <= 2.2))
+    assert np.all((a["hardness"] >= 0) & (a["hardness"] <= 40))
+    assert set(np.unique(a["hbtype"])) <= {0, 1, 2}
+    assert np.all(np.abs(a["poses"][:3]) <= math.pi) and np.all(np.abs(a["poses"][3:]) <= 5)
+
+
+def test_batched_shapes_are_log_uniform_in_range():
+    shapes = synth.batched_shapes(3, 64)
+    assert len(shapes) == 64 and shapes == synth.batched_shapes(3, 64)
+    nl, npro, npo = (np.array(x) for x in zip(*shapes))
+    assert nl.min() >= 8 and nl.max() <= 128
+    assert npro.min() >= 500 and npro.max() <= 5000
+    assert npo.min() >= 1024 and npo.max() <= 65536
+    # log-uniform: the median sits near the geometric mean of the range (8192 poses,
+    # about 1581 protein atoms), not near the arithmetic mean
+    assert 2048 < np.median(npo) < 32768
+    assert 700 < np.median(npro) < 3500
+
+
+def test_he_lattice_is_seeded_and_symmetric():
+    s = synth.make_he_lattice(5, 27)
+    assert s["geom"].shape == (27, 3)
+    np.testing.assert_array_equal(s["dens"], s["dens"].T)
+    assert np.all(np.diff(s["xpnt"]) < 0)   # exponents sorted, largest first
