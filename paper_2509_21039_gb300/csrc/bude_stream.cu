@@ -128,21 +128,36 @@ __global__ void stream_kernel(T* __restrict__ a, T* __restrict__ b, T* __restric
     }
 }
 
-__global__ void dot_finish_kernel(const double* __restrict__ partial, int n, double* __restrict__ out)
+// Sum of the per-CTA partials by one CTA of 1024 threads: each thread adds
+// the partials i = tid, tid + 1024, ... in order, then a butterfly per warp
+// and the 32 warp sums in warp order.  The order is fixed, so the result is
+// deterministic; a serial loop here cost tens of microseconds at 2^25.
+__global__ void __launch_bounds__(1024) dot_finish_kernel(const double* __restrict__ partial, int n,
+                                                          double* __restrict__ out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double v = 0.0;
-        for (int i = 0; i < n; ++i) v += partial[i];
-        *out = v;
+    __shared__ double s_w[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += partial[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w = threadIdx.x < (blockDim.x >> 5) ? s_w[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (threadIdx.x == 0) *out = w;
     }
 }
 
 // f[i,j,k] on interior points; index i*ny*nz + j*nz + k (k fastest).  Each
 // thread owns one (j, k) column for CH consecutive planes of chunk
-// blockIdx.z: its column values u[i0-1 .. i0+CH] sit in registers (each read
-// once), and the j/k neighbours come through the read-only path, where the
-// CTA's tile makes them L1 hits.  No barriers: every load is independent, so
-// many are in flight per SM.
+// blockIdx.z: its column values u[i0-1 .. i0+CH] and the j/k neighbours of
+// its CH points are all loaded before any arithmetic, with the plane index
+// clamped into the array instead of a guard, so that every load of the
+// thread is independent and in flight at once; the stores alone are
+// predicated.  The j/k neighbours come through the read-only path, where the
+// CTA's tile makes most of them L1 hits.  No barriers.
 template <typename T, int TX, int TY, int CH>
 __global__ void __launch_bounds__(TX * TY) laplacian_kernel(const T* __restrict__ u,
                                                             T* __restrict__ f, int nx, int ny,
@@ -154,21 +169,26 @@ __global__ void __launch_bounds__(TX * TY) laplacian_kernel(const T* __restrict_
     if (k >= nz - 1 || j >= ny - 1 || i0 >= i1) return;
     const size_t plane = (size_t)ny * nz;
     const size_t col = (size_t)j * nz + k;
-    T c[CH + 2];
+    T c[CH + 2], yn[CH], yp[CH], zn[CH], zp[CH];
 #pragma unroll
     for (int q = 0; q < CH + 2; ++q) {
-        const int i = i0 - 1 + q;
-        c[q] = (i <= i1) ? __ldg(u + (size_t)i * plane + col) : T(0);
+        const int i = min(i0 - 1 + q, nx - 1);
+        c[q] = __ldg(u + (size_t)i * plane + col);
     }
 #pragma unroll
-    for (int q = 1; q <= CH; ++q) {
-        const int i = i0 - 1 + q;
-        if (i < i1) {
-            const size_t o = (size_t)i * plane + col;
-            f[o] = c[q] * c0 + (c[q - 1] + c[q + 1]) * cx +
-                   (__ldg(u + o - nz) + __ldg(u + o + nz)) * cy +
-                   (__ldg(u + o - 1) + __ldg(u + o + 1)) * cz;
-        }
+    for (int q = 0; q < CH; ++q) {
+        const size_t o = (size_t)min(i0 + q, nx - 1) * plane + col;
+        yn[q] = __ldg(u + o - nz);
+        yp[q] = __ldg(u + o + nz);
+        zn[q] = __ldg(u + o - 1);
+        zp[q] = __ldg(u + o + 1);
+    }
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+        const int i = i0 + q;
+        if (i < i1)
+            f[(size_t)i * plane + col] = c[q + 1] * c0 + (c[q] + c[q + 2]) * cx +
+                                         (yn[q] + yp[q]) * cy + (zn[q] + zp[q]) * cz;
     }
 }
 
@@ -211,7 +231,7 @@ cudaError_t stream_launch(int op, T* a, T* b, T* c, T s, long long n, double* do
     cudaError_t e = cudaGetLastError();
     *launches = 1;
     if (e == cudaSuccess && op == kDot) {
-        dot_finish_kernel<<<1, 32, 0, st>>>(partial, (int)grid, dot_out);
+        dot_finish_kernel<<<1, 1024, 0, st>>>(partial, (int)grid, dot_out);
         e = cudaGetLastError();
         *launches = 2;
     }
@@ -222,7 +242,7 @@ template <typename T>
 cudaError_t laplacian_launch(const T* u, T* f, int nx, int ny, int nz, T cx, T cy, T cz, T c0,
                              cudaStream_t st)
 {
-    constexpr int TX = 32, TY = 8, CH = 8;
+    constexpr int TX = 64, TY = 4, CH = 8;
     dim3 grid((unsigned)((nz - 2 + TX - 1) / TX), (unsigned)((ny - 2 + TY - 1) / TY),
               (unsigned)((nx - 2 + CH - 1) / CH));
     laplacian_kernel<T, TX, TY, CH><<<grid, dim3(TX, TY), 0, st>>>(u, f, nx, ny, nz, cx, cy, cz, c0);
