@@ -253,6 +253,13 @@ def test_bad_options_are_rejected():
 
 # --- full-size workload: every pose computed, a sample checked --------------
 
+def _bench_options(variant, n_lig, n_pro, n_poses, mode="plain"):
+    # the launch configuration bench.py times: the tuned shape for this workload
+    from paper_2509_21039_gb300 import tune
+    o = tune.lookup(variant, n_lig, n_pro, n_poses, mode=mode)
+    return o if o is not None else bude.LaunchOptions(variant=variant)
+
+
 def test_full_size_sampled_against_oracle():
     D = synth.make_deck(1, **synth.FULL)
     deck = bude.Deck(D, device=DEV)
@@ -261,11 +268,49 @@ def test_full_size_sampled_against_oracle():
     idx = np.sort(rng.choice(D["poses"].shape[1], 48, replace=False))
     idx[-1] = D["poses"].shape[1] - 1
     ref, A = oracle.energies(D, D["poses"][:, idx], n_threads=-1, with_abs=True)
+    n = D["poses"].shape[1]
     for v in ("ieee", "fast", "comp"):
-        E = bude.energies(deck, P, variant=v).cpu().numpy()
-        assert np.isfinite(E).all()
-        err = scaled_error(E[idx], ref, A)
-        assert err.max() <= GATE[v], (v, err.max())
+        for mode in ("plain", "cull"):
+            o = _bench_options(v, 64, 2672, n, mode)
+            E = bude.energies(deck, P, opts=o).cpu().numpy()
+            assert np.isfinite(E).all()
+            err = scaled_error(E[idx], ref, A)
+            assert err.max() <= GATE[v], (v, mode, err.max())
+
+
+def test_flat_work_index_beyond_2_pow_31():
+    # 2^22 poses of the full deck: the flat space (tiles x 64 x 2672 pairs) is
+    # about 2.8e9 iterations, past 32-bit indexing; sampled against the oracle,
+    # the last pose included
+    D = synth.make_deck(9, 64, 2672, 34, 1 << 22)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    o = _bench_options("fast", 64, 2672, 65536)
+    tiles = -(-P.shape[1] // (32 * o.ppwi))
+    assert tiles * 64 * 2672 > 2 ** 31
+    E = bude.energies(deck, P, opts=o).cpu().numpy()
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(P.shape[1], 40, replace=False))
+    idx[-1] = P.shape[1] - 1
+    ref, A = oracle.energies(D, D["poses"][:, idx], n_threads=-1, with_abs=True)
+    assert np.isfinite(E).all()
+    assert scaled_error(E[idx], ref, A).max() <= GATE["fast"]
+    deck.close()
+
+
+def test_long_protein_many_ligand_atoms():
+    # 60000 protein atoms cannot be staged at once: many chunks per tile, and
+    # 300 ligand rows in the warp split's cost prefix
+    D = synth.make_deck(10, 300, 60000, 34, 300)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    idx = np.arange(0, 300, 5)
+    ref, A = oracle.energies(D, D["poses"][:, idx], n_threads=-1, with_abs=True)
+    for kw in (dict(variant="ieee", ppwi=8, block=512), dict(variant="fast", ppwi=16, block=384),
+               dict(variant="comp", ppwi=2, block=256, cull=1)):
+        E = bude.energies(deck, P, opts=bude.LaunchOptions(**kw)).cpu().numpy()
+        assert scaled_error(E[idx], ref, A).max() <= GATE[kw["variant"]], kw
+    deck.close()
 
 
 # --- batched --------------------------------------------------------------
