@@ -10,8 +10,13 @@
 // precomputes, for every atom pair and primitive pair, the Gaussian product
 // p = x_a + x_b, P = (x_a A + x_b B)/p and K = c_a c_b N_a N_b
 // exp(-x_a x_b |A-B|^2/p), and the Schwarz bound Q_ij = sqrt((ij|ij)); a
-// quartet with Q_ij Q_kl below the caller's threshold is skipped.  Primitive
-// quartets then cost
+// quartet with Q_ij Q_kl below the caller's threshold is skipped.  The pairs
+// are kept sorted by Q (descending), so for the pair of rank a the partners
+// that survive the threshold are the ranks b < min(a + 1, c_a) for a count c_a
+// found by binary search.  Each call turns the counts into a prefix sum and
+// hands out the surviving quartets, and only those, one per thread: no lane
+// idles on a screened quartet and no index is decoded with a square root.
+// Primitive quartets then cost
 //   (ab|cd) = K_ab K_cd 2 pi^(5/2) / (p q sqrt(p+q)) F0(p q / (p+q) |P-Q|^2)
 // with F0(t) = sqrt(pi/t) erf(sqrt t) / 2.  GB300's FP64 units are a small
 // fraction of its FP32 ones, so besides the FP64 kernel there is one that
@@ -20,6 +25,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "bude_internal.h"
 
@@ -35,6 +41,9 @@ struct HfPlanDev {
     const float4* pqf;    // FP32 copies
     const float* kpf;
     const double* schwarz;  // [m]
+    const int2* pairs;      // [m] (i, j), i >= j
+    const int* order;       // [m] pair index by rank of Q, largest first
+    const double* qsorted;  // [m] Q by rank
 };
 
 __device__ __forceinline__ void pair_of(long long ij, int* i, int* j)
@@ -144,26 +153,89 @@ __global__ void hf_schwarz_kernel(const HfPlanDev P, double* __restrict__ q)
         q[ij] = sqrt(fabs(contracted_f64(P, ij, ij)));
 }
 
-// One thread per unique quartet (IJ >= KL), grid-stride.
-template <bool F32>
-__global__ void hf_fock_kernel(const HfPlanDev P, const double* __restrict__ D,
-                               double* __restrict__ F, double tol)
+// (i, j) of every pair, once per plan.
+__global__ void hf_pair_table_kernel(long long m, int2* __restrict__ pairs)
 {
-    const long long nq = P.m * (P.m + 1) / 2;
+    for (long long ij = blockIdx.x * (long long)blockDim.x + threadIdx.x; ij < m;
+         ij += (long long)gridDim.x * blockDim.x) {
+        int i, j;
+        pair_of(ij, &i, &j);
+        pairs[ij] = make_int2(i, j);
+    }
+}
+
+// w[a] = number of surviving partners b <= a of the pair of rank a: the ranks
+// b < c_a with Q_b Q_a >= tol (a prefix, Q being sorted descending), capped at
+// a + 1 so that every unordered quartet is counted once.
+__global__ void hf_count_kernel(const HfPlanDev P, double tol, long long* __restrict__ w)
+{
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < P.m;
+         a += (long long)gridDim.x * blockDim.x) {
+        const double qa = P.qsorted[a];
+        long long lo = 0, hi = a + 1;  // count in [0, a + 1]
+        while (lo < hi) {
+            const long long mid = (lo + hi) >> 1;
+            if (P.qsorted[mid] * qa >= tol) lo = mid + 1; else hi = mid;
+        }
+        w[a] = lo;
+    }
+}
+
+// In-place exclusive prefix sum of w[0..m) into prefix[0..m] by one CTA of
+// 1024 threads: each thread scans a contiguous slice, the slice totals are
+// scanned in shared memory, and prefix[m] is the number of quartets.
+__global__ void __launch_bounds__(1024) hf_scan_kernel(const long long* __restrict__ w, long long m,
+                                                      long long* __restrict__ prefix)
+{
+    __shared__ long long s_tot[1024];
+    const int t = threadIdx.x;
+    const long long per = (m + blockDim.x - 1) / blockDim.x;
+    const long long b0 = min(m, (long long)t * per), b1 = min(m, b0 + per);
+    long long sum = 0;
+    for (long long a = b0; a < b1; ++a) sum += w[a];
+    s_tot[t] = sum;
+    __syncthreads();
+    if (t == 0) {
+        long long run = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            const long long v = s_tot[k];
+            s_tot[k] = run;
+            run += v;
+        }
+        prefix[m] = run;
+    }
+    __syncthreads();
+    long long run = s_tot[t];
+    for (long long a = b0; a < b1; ++a) {
+        prefix[a] = run;
+        run += w[a];
+    }
+}
+
+// One thread per surviving quartet: work item x lies in the rank a with
+// prefix[a] <= x < prefix[a + 1] and pairs with rank b = x - prefix[a].
+template <bool F32>
+__global__ void hf_fock_kernel(const HfPlanDev P, const long long* __restrict__ prefix,
+                               const double* __restrict__ D, double* __restrict__ F)
+{
+    const long long total = prefix[P.m];
     const int n = P.n;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
-         q += (long long)gridDim.x * blockDim.x) {
-        int IJ_, KL_;
-        pair_of(q, &IJ_, &KL_);
-        const long long IJ = IJ_, KL = KL_;
-        if (P.schwarz[IJ] * P.schwarz[KL] < tol) continue;
-        int i, j, k, l;
-        pair_of(IJ, &i, &j);
-        pair_of(KL, &k, &l);
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+         x += (long long)gridDim.x * blockDim.x) {
+        long long lo = 0, hi = P.m - 1;  // largest a with prefix[a] <= x
+        while (lo < hi) {
+            const long long mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= x) lo = mid; else hi = mid - 1;
+        }
+        const long long a = lo, b = x - prefix[a];
+        const long long IJ = P.order[a], KL = P.order[b];
+        const int2 pij = P.pairs[IJ], pkl = P.pairs[KL];
+        const int i = pij.x, j = pij.y, k = pkl.x, l = pkl.y;
         double v = F32 ? (double)contracted_f32(P, IJ, KL) : contracted_f64(P, IJ, KL);
         if (i == j) v *= 0.5;
         if (k == l) v *= 0.5;
-        if (IJ == KL) v *= 0.5;
+        if (a == b) v *= 0.5;
+        // the six updates are symmetric under (ij) <-> (kl) once G = F + F^T
         atomicAdd(F + (size_t)i * n + j, 4.0 * D[(size_t)k * n + l] * v);
         atomicAdd(F + (size_t)k * n + l, 4.0 * D[(size_t)i * n + j] * v);
         atomicAdd(F + (size_t)i * n + k, -D[(size_t)j * n + l] * v);
@@ -199,6 +271,11 @@ struct bude_hf {
     float* kpf = nullptr;
     double* schwarz = nullptr;
     double* fock = nullptr;  // [n][n] accumulation buffer
+    int2* pairs = nullptr;       // [m]
+    int* order = nullptr;        // [m]
+    double* qsorted = nullptr;   // [m]
+    long long* counts = nullptr; // [m] per-call survivor counts
+    long long* prefix = nullptr; // [m + 1]
     HfPlanDev view() const
     {
         HfPlanDev v;
@@ -210,6 +287,9 @@ struct bude_hf {
         v.pqf = pqf;
         v.kpf = kpf;
         v.schwarz = schwarz;
+        v.pairs = pairs;
+        v.order = order;
+        v.qsorted = qsorted;
         return v;
     }
 };
@@ -227,6 +307,11 @@ extern "C" BUDE_API int bude_hf_destroy(bude_hf* h)
     cudaFree(h->kpf);
     cudaFree(h->schwarz);
     cudaFree(h->fock);
+    cudaFree(h->pairs);
+    cudaFree(h->order);
+    cudaFree(h->qsorted);
+    cudaFree(h->counts);
+    cudaFree(h->prefix);
     delete h;
     return BUDE_OK;
 }
@@ -260,7 +345,12 @@ extern "C" BUDE_API int bude_hf_create(int32_t n_atoms, const double* geom, int3
         dev_alloc((void**)&h->pqf, e * sizeof(float4)) ||
         dev_alloc((void**)&h->kpf, e * sizeof(float)) ||
         dev_alloc((void**)&h->schwarz, (size_t)h->m * sizeof(double)) ||
-        dev_alloc((void**)&h->fock, (size_t)n_atoms * n_atoms * sizeof(double)))
+        dev_alloc((void**)&h->fock, (size_t)n_atoms * n_atoms * sizeof(double)) ||
+        dev_alloc((void**)&h->pairs, (size_t)h->m * sizeof(int2)) ||
+        dev_alloc((void**)&h->order, (size_t)h->m * sizeof(int)) ||
+        dev_alloc((void**)&h->qsorted, (size_t)h->m * sizeof(double)) ||
+        dev_alloc((void**)&h->counts, (size_t)h->m * sizeof(long long)) ||
+        dev_alloc((void**)&h->prefix, ((size_t)h->m + 1) * sizeof(long long)))
         return bail(BUDE_ERR_OOM);
     // host inputs: copied synchronously (plan creation is not on the hot path)
     if (cudaMemcpy(h->geom, geom, 3 * sizeof(double) * n_atoms, cudaMemcpyHostToDevice) ||
@@ -272,8 +362,23 @@ extern "C" BUDE_API int bude_hf_create(int32_t n_atoms, const double* geom, int3
         n_atoms, ngauss, h->geom, h->xc, h->xc + ngauss, h->pq, h->kp, h->pqf, h->kpf);
     const long long sb = std::min<long long>(4096, (h->m + 127) / 128);
     hf_schwarz_kernel<<<(unsigned)std::max(1ll, sb), 128, 0, s>>>(h->view(), h->schwarz);
+    hf_pair_table_kernel<<<(unsigned)std::max(1ll, sb), 128, 0, s>>>(h->m, h->pairs);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
         return bail(BUDE_ERR_CUDA);
+    // rank the pairs by their Schwarz bound, largest first (once per plan)
+    {
+        std::vector<double> q((size_t)h->m);
+        if (cudaMemcpy(q.data(), h->schwarz, (size_t)h->m * sizeof(double), cudaMemcpyDeviceToHost))
+            return bail(BUDE_ERR_CUDA);
+        std::vector<int> ord((size_t)h->m);
+        for (long long k = 0; k < h->m; ++k) ord[(size_t)k] = (int)k;
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return q[x] > q[y]; });
+        std::vector<double> qs((size_t)h->m);
+        for (long long k = 0; k < h->m; ++k) qs[(size_t)k] = q[(size_t)ord[(size_t)k]];
+        if (cudaMemcpy(h->order, ord.data(), (size_t)h->m * sizeof(int), cudaMemcpyHostToDevice) ||
+            cudaMemcpy(h->qsorted, qs.data(), (size_t)h->m * sizeof(double), cudaMemcpyHostToDevice))
+            return bail(BUDE_ERR_CUDA);
+    }
     *out = h;
     return BUDE_OK;
 }
@@ -290,12 +395,15 @@ extern "C" BUDE_API int bude_hf_fock(bude_hf* h, const double* dens, double* g, 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long nq = h->m * (h->m + 1) / 2;
-    const long long blocks = std::max(1ll, std::min<long long>((long long)sms * 16, (nq + 127) / 128));
+    // surviving quartets: counts per rank, their prefix sum, then one thread each
+    const long long cb = std::max(1ll, std::min<long long>(4096, (h->m + 255) / 256));
+    hf_count_kernel<<<(unsigned)cb, 256, 0, s>>>(h->view(), tol, h->counts);
+    hf_scan_kernel<<<1, 1024, 0, s>>>(h->counts, h->m, h->prefix);
+    const unsigned blocks = (unsigned)sms * 16;
     if (variant == BUDE_FP64)
-        hf_fock_kernel<false><<<(unsigned)blocks, 128, 0, s>>>(h->view(), dens, h->fock, tol);
+        hf_fock_kernel<false><<<blocks, 128, 0, s>>>(h->view(), h->prefix, dens, h->fock);
     else
-        hf_fock_kernel<true><<<(unsigned)blocks, 128, 0, s>>>(h->view(), dens, h->fock, tol);
+        hf_fock_kernel<true><<<blocks, 128, 0, s>>>(h->view(), h->prefix, dens, h->fock);
     const long long sb = std::max(1ll, std::min<long long>(4096, ((long long)nn + 255) / 256));
     hf_symmetrise_kernel<<<(unsigned)sb, 256, 0, s>>>(h->fock, g, h->n);
     return cudaGetLastError() == cudaSuccess ? BUDE_OK : BUDE_ERR_CUDA;
