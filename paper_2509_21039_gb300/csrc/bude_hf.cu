@@ -18,7 +18,11 @@
 // idles on a screened quartet and no index is decoded with a square root.
 // Primitive quartets then cost
 //   (ab|cd) = K_ab K_cd 2 pi^(5/2) / (p q sqrt(p+q)) F0(p q / (p+q) |P-Q|^2)
-// with F0(t) = sqrt(pi/t) erf(sqrt t) / 2.  GB300's FP64 units are a small
+// with F0(t) = sqrt(pi/t) erf(sqrt t) / 2.  With rho = p q / (p+q) this is
+//   K'_ab K'_cd sqrt(rho) erf(x) / x,   x = sqrt(rho) |P-Q|,
+//   K' = K pi^(3/2) p^(-3/2),   sqrt(rho) = 1 / sqrt(1/p + 1/q),
+// so a primitive quartet costs two reciprocal roots and an erf, with no
+// division; the plan stores 1/p and K' per primitive pair.  GB300's FP64 units are a small
 // fraction of its FP32 ones, so besides the FP64 kernel there is one that
 // evaluates the primitive integrals in FP32 and accumulates the Fock matrix
 // in FP64.
@@ -36,14 +40,21 @@ constexpr double kPi = 3.14159265358979323846;
 struct HfPlanDev {
     int n, ng;
     long long m;          // unique pairs n(n+1)/2
-    const double4_32a* pq;    // [m][ng*ng] {Px, Py, Pz, p}
-    const double* kp;     // [m][ng*ng] K
+    const double4_32a* pq;    // [m][ng*ng] {Px, Py, Pz, 1/p}
+    const double* kp;     // [m][ng*ng] K' = K pi^(3/2) p^(-3/2)
     const float4* pqf;    // FP32 copies
     const float* kpf;
     const double* schwarz;  // [m]
     const int2* pairs;      // [m] (i, j), i >= j
     const int* order;       // [m] pair index by rank of Q, largest first
     const double* qsorted;  // [m] Q by rank
+    // the primitive products again, by rank and primitive-pair-major
+    // ([ng*ng][m]), so that the lanes of a warp, which hold consecutive ranks,
+    // read adjacent words
+    const double4_32a* rpq;
+    const double* rkp;
+    const float4* rpqf;
+    const float* rkpf;
 };
 
 __device__ __forceinline__ void pair_of(long long ij, int* i, int* j)
@@ -78,71 +89,104 @@ __global__ void hf_pairs_kernel(int n, int ng, const double* __restrict__ geom,
         }
         const double na = pow(2.0 * xa / kPi, 0.75), nb = pow(2.0 * xb / kPi, 0.75);
         const double K = coef[a] * coef[b] * na * nb * exp(-xa * xb * r2 / p);
-        pq[e] = make_double4_32a(P[0], P[1], P[2], p);
-        kp[e] = K;
-        pqf[e] = make_float4((float)P[0], (float)P[1], (float)P[2], (float)p);
-        kpf[e] = (float)K;
+        const double Kp = K * pow(kPi / p, 1.5);
+        pq[e] = make_double4_32a(P[0], P[1], P[2], 1.0 / p);
+        kp[e] = Kp;
+        pqf[e] = make_float4((float)P[0], (float)P[1], (float)P[2], (float)(1.0 / p));
+        kpf[e] = (float)Kp;
     }
 }
 
-__device__ __forceinline__ double boys0(double t)
+// erf(x) / x from x^2, finite at x = 0 (2 / sqrt(pi)): the argument is
+// floored far below any x^2 that matters, where erf(x) = 2x/sqrt(pi) to full
+// precision, so that both reciprocal roots stay finite.
+__device__ __forceinline__ double erf_over_x(double x2)
 {
-    if (t < 1e-10) return 1.0 - t / 3.0;
-    const double st = sqrt(t);
-    return 0.5 * sqrt(kPi / t) * erf(st);
+    const double y = fmax(x2, 1e-300);
+    const double r = rsqrt(y);
+    return erf(y * r) * r;
 }
-__device__ __forceinline__ float boys0f(float t)
+__device__ __forceinline__ float erf_over_x(float x2)
 {
-    if (t < 1e-5f) return 1.0f - t / 3.0f;
-    const float st = sqrtf(t);
-    return 0.5f * sqrtf((float)kPi / t) * erff(st);
+    const float y = fmaxf(x2, 1e-30f);
+    const float r = rsqrtf(y);
+    return erff(y * r) * r;
 }
 
+// Precision-matched helpers for the template below (declared before it, so
+// that the float instantiation never promotes to double).
+__device__ __forceinline__ float hf_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double hf_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float hf_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double hf_fma(double a, double b, double c) { return fma(a, b, c); }
+
 // Contracted (ij|kl) from the two pairs' primitive products.
+template <typename T, typename T4>
+__device__ __forceinline__ T contracted(const T4* __restrict__ A, const T4* __restrict__ C,
+                                        const T* __restrict__ KA, const T* __restrict__ KC, int g2)
+{
+    T v = 0;
+    for (int ab = 0; ab < g2; ++ab) {
+        const T4 a = A[ab];
+        const T ka = KA[ab];
+        T w = 0;
+        for (int cd = 0; cd < g2; ++cd) {
+            const T4 c = C[cd];
+            const T dx = a.x - c.x, dy = a.y - c.y, dz = a.z - c.z;
+            const T r2 = hf_fma(dz, dz, hf_fma(dy, dy, dx * dx));
+            const T rs = hf_rsqrt(a.w + c.w);   // sqrt(rho)
+            w = hf_fma(KC[cd] * rs, erf_over_x(r2 * rs * rs), w);
+        }
+        v = hf_fma(ka, w, v);
+    }
+    return v;
+}
+
+// The same over the rank-ordered copies: primitive pair ab of rank a is at
+// [ab * m + a].
+template <typename T, typename T4>
+__device__ __forceinline__ T contracted_ranked(const T4* __restrict__ pq, const T* __restrict__ kp,
+                                               long long m, long long a, long long b, int g2)
+{
+    T v = 0;
+    for (int ab = 0; ab < g2; ++ab) {
+        const T4 x = pq[ab * m + a];
+        const T ka = kp[ab * m + a];
+        T w = 0;
+        for (int cd = 0; cd < g2; ++cd) {
+            const T4 c = pq[cd * m + b];
+            const T dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;
+            const T r2 = hf_fma(dz, dz, hf_fma(dy, dy, dx * dx));
+            const T rs = hf_rsqrt(x.w + c.w);   // sqrt(rho)
+            w = hf_fma(kp[cd * m + b] * rs, erf_over_x(r2 * rs * rs), w);
+        }
+        v = hf_fma(ka, w, v);
+    }
+    return v;
+}
+
+// Gather of the primitive products into the rank-ordered copies.
+__global__ void hf_rank_copy_kernel(const HfPlanDev P, double4_32a* __restrict__ rpq,
+                                    double* __restrict__ rkp, float4* __restrict__ rpqf,
+                                    float* __restrict__ rkpf)
+{
+    const int g2 = P.ng * P.ng;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < P.m * g2;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long ab = e / P.m, a = e % P.m;
+        const long long src = (long long)P.order[a] * g2 + ab;
+        rpq[e] = P.pq[src];
+        rkp[e] = P.kp[src];
+        rpqf[e] = P.pqf[src];
+        rkpf[e] = P.kpf[src];
+    }
+}
+
 __device__ double contracted_f64(const HfPlanDev& P, long long ij, long long kl)
 {
     const int g2 = P.ng * P.ng;
-    const double4_32a* A = P.pq + ij * g2;
-    const double4_32a* C = P.pq + kl * g2;
-    const double* KA = P.kp + ij * g2;
-    const double* KC = P.kp + kl * g2;
-    double v = 0.0;
-    for (int ab = 0; ab < g2; ++ab) {
-        const double4_32a a = A[ab];
-        const double ka = KA[ab];
-        for (int cd = 0; cd < g2; ++cd) {
-            const double4_32a c = C[cd];
-            const double dx = a.x - c.x, dy = a.y - c.y, dz = a.z - c.z;
-            const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-            const double pq = a.w * c.w, s = a.w + c.w;
-            v += ka * KC[cd] * (2.0 * 17.493418327624862 /* pi^(5/2) */) / (pq * sqrt(s)) *
-                 boys0(pq / s * r2);
-        }
-    }
-    return v;
-}
-
-__device__ float contracted_f32(const HfPlanDev& P, long long ij, long long kl)
-{
-    const int g2 = P.ng * P.ng;
-    const float4* A = P.pqf + ij * g2;
-    const float4* C = P.pqf + kl * g2;
-    const float* KA = P.kpf + ij * g2;
-    const float* KC = P.kpf + kl * g2;
-    float v = 0.f;
-    for (int ab = 0; ab < g2; ++ab) {
-        const float4 a = A[ab];
-        const float ka = KA[ab];
-        for (int cd = 0; cd < g2; ++cd) {
-            const float4 c = C[cd];
-            const float dx = a.x - c.x, dy = a.y - c.y, dz = a.z - c.z;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float pq = a.w * c.w, s = a.w + c.w;
-            v = fmaf(ka * KC[cd] * (float)(2.0 * 17.493418327624862) / (pq * sqrtf(s)),
-                     boys0f(pq / s * r2), v);
-        }
-    }
-    return v;
+    return contracted<double, double4_32a>(P.pq + ij * g2, P.pq + kl * g2, P.kp + ij * g2,
+                                           P.kp + kl * g2, g2);
 }
 
 // Schwarz bounds Q_ij = sqrt((ij|ij)) in FP64.
@@ -231,12 +275,27 @@ __global__ void hf_fock_kernel(const HfPlanDev P, const long long* __restrict__ 
         const long long IJ = P.order[a], KL = P.order[b];
         const int2 pij = P.pairs[IJ], pkl = P.pairs[KL];
         const int i = pij.x, j = pij.y, k = pkl.x, l = pkl.y;
-        double v = F32 ? (double)contracted_f32(P, IJ, KL) : contracted_f64(P, IJ, KL);
+        const int g2 = P.ng * P.ng;
+        double v = F32 ? (double)contracted_ranked<float, float4>(P.rpqf, P.rkpf, P.m, a, b, g2)
+                       : contracted_ranked<double, double4_32a>(P.rpq, P.rkp, P.m, a, b, g2);
         if (i == j) v *= 0.5;
         if (k == l) v *= 0.5;
         if (a == b) v *= 0.5;
-        // the six updates are symmetric under (ij) <-> (kl) once G = F + F^T
-        atomicAdd(F + (size_t)i * n + j, 4.0 * D[(size_t)k * n + l] * v);
+        // the six updates are symmetric under (ij) <-> (kl) once G = F + F^T.
+        // Consecutive work items mostly share the rank a, so a full warp on one
+        // (ij) adds its F_ij terms in registers first: 32 atomics on one
+        // address would serialise.
+        const double cij = 4.0 * D[(size_t)k * n + l] * v;
+        const unsigned act = __activemask();
+        const long long a0 = __shfl_sync(act, a, 0);
+        if (act == 0xffffffffu && __all_sync(act, a == a0)) {
+            double t = cij;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if ((threadIdx.x & 31) == 0) atomicAdd(F + (size_t)i * n + j, t);
+        } else {
+            atomicAdd(F + (size_t)i * n + j, cij);
+        }
         atomicAdd(F + (size_t)k * n + l, 4.0 * D[(size_t)i * n + j] * v);
         atomicAdd(F + (size_t)i * n + k, -D[(size_t)j * n + l] * v);
         atomicAdd(F + (size_t)i * n + l, -D[(size_t)j * n + k] * v);
@@ -276,6 +335,10 @@ struct bude_hf {
     double* qsorted = nullptr;   // [m]
     long long* counts = nullptr; // [m] per-call survivor counts
     long long* prefix = nullptr; // [m + 1]
+    double4_32a* rpq = nullptr;  // rank-ordered copies, [ng*ng][m]
+    double* rkp = nullptr;
+    float4* rpqf = nullptr;
+    float* rkpf = nullptr;
     HfPlanDev view() const
     {
         HfPlanDev v;
@@ -290,6 +353,10 @@ struct bude_hf {
         v.pairs = pairs;
         v.order = order;
         v.qsorted = qsorted;
+        v.rpq = rpq;
+        v.rkp = rkp;
+        v.rpqf = rpqf;
+        v.rkpf = rkpf;
         return v;
     }
 };
@@ -312,6 +379,10 @@ extern "C" BUDE_API int bude_hf_destroy(bude_hf* h)
     cudaFree(h->qsorted);
     cudaFree(h->counts);
     cudaFree(h->prefix);
+    cudaFree(h->rpq);
+    cudaFree(h->rkp);
+    cudaFree(h->rpqf);
+    cudaFree(h->rkpf);
     delete h;
     return BUDE_OK;
 }
@@ -350,7 +421,11 @@ extern "C" BUDE_API int bude_hf_create(int32_t n_atoms, const double* geom, int3
         dev_alloc((void**)&h->order, (size_t)h->m * sizeof(int)) ||
         dev_alloc((void**)&h->qsorted, (size_t)h->m * sizeof(double)) ||
         dev_alloc((void**)&h->counts, (size_t)h->m * sizeof(long long)) ||
-        dev_alloc((void**)&h->prefix, ((size_t)h->m + 1) * sizeof(long long)))
+        dev_alloc((void**)&h->prefix, ((size_t)h->m + 1) * sizeof(long long)) ||
+        dev_alloc((void**)&h->rpq, e * sizeof(double4_32a)) ||
+        dev_alloc((void**)&h->rkp, e * sizeof(double)) ||
+        dev_alloc((void**)&h->rpqf, e * sizeof(float4)) ||
+        dev_alloc((void**)&h->rkpf, e * sizeof(float)))
         return bail(BUDE_ERR_OOM);
     // host inputs: copied synchronously (plan creation is not on the hot path)
     if (cudaMemcpy(h->geom, geom, 3 * sizeof(double) * n_atoms, cudaMemcpyHostToDevice) ||
@@ -379,6 +454,10 @@ extern "C" BUDE_API int bude_hf_create(int32_t n_atoms, const double* geom, int3
             cudaMemcpy(h->qsorted, qs.data(), (size_t)h->m * sizeof(double), cudaMemcpyHostToDevice))
             return bail(BUDE_ERR_CUDA);
     }
+    hf_rank_copy_kernel<<<(unsigned)std::max(1ll, blocks), 256, 0, s>>>(h->view(), h->rpq, h->rkp,
+                                                                        h->rpqf, h->rkpf);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return bail(BUDE_ERR_CUDA);
     *out = h;
     return BUDE_OK;
 }

@@ -151,7 +151,7 @@ def test_hartree_fock_plan_allocation_failures():
     dens = torch.from_numpy(S["dens"]).to(DEV)
     ref = bude.HartreeFock(S["geom"], S["xpnt"], S["coef"], device=DEV).fock(dens).cpu().numpy()
     fails = oks = 0
-    for k in range(1, 18):
+    for k in range(1, 24):
         bude.debug_fail_alloc(k)
         try:
             hf = bude.HartreeFock(S["geom"], S["xpnt"], S["coef"], device=DEV)
