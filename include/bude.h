@@ -146,8 +146,9 @@ BUDE_API int bude_deck_info(const bude_deck* deck, int32_t* n_lig, int32_t* n_pr
  * opts:     NULL for defaults.
  * n = 0 is a no-op.  A deck with no ligand or no protein atoms yields zeros.
  * A pose whose transform has a NaN yields NaN.  The first call with a larger
- * n than before grows the deck's workspace with stream-ordered allocation;
- * make such a call before capturing the stream into a CUDA graph.
+ * n than before grows the deck's workspace: it synchronises "stream" when it
+ * replaces a smaller workspace and allocates with cudaMalloc, so make such a
+ * call before capturing the stream into a CUDA graph.
  */
 BUDE_API int bude_energies(bude_deck* deck, const float* poses, int64_t n,
                   float* energies, const bude_options* opts, void* stream);
