@@ -340,21 +340,23 @@ def cull_throughput(bude, tune, deck, poses, out, ms_brute, timed, variant="fast
             "note": "pairs beyond R + 4 A are skipped warp-wide; not an Eq. 3 FLOP rate"}
 
 
-def param_grad_throughput(bude, synth, dev, timed, variant="fast"):
+def param_grad_throughput(bude, synth, tune, dev, timed, variant="fast"):
     """Gradient of the pose-energy sum w.r.t. ligand coordinates and forcefield
     parameters over 16384 poses of the 64 x 2672 deck."""
     import torch
     D = synth.make_deck(4, **synth.GRAD)
     deck = bude.Deck(D, device=dev)
     P = torch.from_numpy(D["poses"]).to(dev)
-    o = bude.LaunchOptions(variant=variant, ppwi=4, block=256)
+    o = tune.lookup(variant, 64, 2672, D["poses"].shape[1], mode="param") or \
+        bude.LaunchOptions(variant=variant, ppwi=8, block=384)
     ms, launches = timed(lambda: bude.param_grad(deck, P, opts=o), 5, 2)
     deck.close()
     t = statistics.mean(ms)
     return {"workload": "dL/d(ligand xyz, radius, hardness, elsc), L = sum of 16384 pose "
                         "energies, 64 lig x 2672 pro, seed 4",
             "variant": variant, "ms": t, "poses_per_s": P.shape[1] / (t / 1e3),
-            "kernels_per_call": launches // 5}
+            "kernels_per_call": launches // 5,
+            "opts": {"ppwi": o.ppwi, "block": o.block, "ctas_per_sm": o.ctas_per_sm}}
 
 
 def hbm_calibration(bude, dev, timed, peak_gbs):
@@ -611,7 +613,7 @@ def main():
         line["batched"] = batched_vs_plain(bude, synth, tune, dev, timed)
         line["adjoint"] = adjoint_throughput(bude, synth, tune, dev, timed)
         line["refine"] = refine_throughput(bude, synth, tune, dev, timed)
-        line["param_grad"] = param_grad_throughput(bude, synth, dev, timed)
+        line["param_grad"] = param_grad_throughput(bude, synth, tune, dev, timed)
         line["hbm_calibration"] = hbm_calibration(bude, dev, timed,
                                                   peaks.get("hbm_gbs", 6800.0))
         line["hartree_fock"] = hartree_fock(bude, synth, dev, timed)

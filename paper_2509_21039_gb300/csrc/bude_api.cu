@@ -1089,9 +1089,10 @@ extern "C" BUDE_API int bude_param_grad(bude_deck* deck, const float* poses, int
     const DeviceInfo di = device_info(dev);
     const size_t budget = smem_budget(di, r.cps);
     const size_t fixed = param_smem_bytes(r.P, deck->n_lig, deck->n_rows, deck->n_types, 0);
-    if (fixed + 16 * 32 > budget)
+    const size_t atom_bytes = (size_t)param_atom_bytes(r.P);
+    if (fixed + atom_bytes * 32 > budget)
         return fail(BUDE_ERR_UNSUPPORTED, "gradient accumulators and pair table do not fit in shared memory");
-    int chunk = (int)std::min<size_t>((size_t)deck->n_pro, (budget - fixed) / 16);
+    int chunk = (int)std::min<size_t>((size_t)deck->n_pro, (budget - fixed) / atom_bytes);
     if (r.tile > 0) chunk = std::min(chunk, r.tile);
     const size_t smem = param_smem_bytes(r.P, deck->n_lig, deck->n_rows, deck->n_types, chunk);
     CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),

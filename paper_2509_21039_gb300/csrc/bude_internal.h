@@ -56,6 +56,9 @@ struct ParamArgs {
     int n_lig, n_pro, n_types, n_rows, chunk;
 };
 const void* kernel_param(int variant, int P);
+// Shared-memory bytes per staged protein atom of param_kernel: the packed
+// kernels (even P) duplicate each coordinate into both halves of an FP32x2 pair.
+__host__ __device__ constexpr int param_atom_bytes(int P) { return P % 2 == 0 ? 32 : 16; }
 size_t param_smem_bytes(int P, int n_lig, int n_rows, int n_types, int chunk);
 cudaError_t launch_param_reduce(const double* cta_acc, int n_cta, int n_lig, int n_rows,
                                 int n_types, double* sums, const int* row_type, const float4* ff,

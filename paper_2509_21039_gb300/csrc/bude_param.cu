@@ -14,6 +14,8 @@
 // type) pair.  The ligand gradient R^T g is summed per ligand atom.  A second
 // pass adds the CTAs' accumulators in CTA order and applies the combination
 // rules (R = r_a + r_b, H = (h_a + h_b)/2, C_E = K_E q_a q_b w_ab).
+#include <type_traits>
+
 #include "bude_internal.h"
 
 namespace bude {
@@ -29,6 +31,9 @@ template <int V, int P>
 __global__ void param_kernel(const ParamArgs a)
 {
     constexpr int TP = 32 * P;
+    // even P: two poses per FP32x2 instruction, the pair record read once per
+    // same-type run, and the desolvation terms left out on runs where S = 0
+    constexpr bool PACK = P % 2 == 0;
     extern __shared__ __align__(16) unsigned char smem[];
     const int W = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5;
@@ -105,7 +110,15 @@ __global__ void param_kernel(const ParamArgs a)
             if (q != staged_chunk) {
                 __syncthreads();
                 const float4* gsrc = a.pro + (size_t)q * CL;
-                for (int i = threadIdx.x; i < len_q; i += blockDim.x) s_pro[i] = gsrc[i];
+                for (int i = threadIdx.x; i < len_q; i += blockDim.x) {
+                    const float4 v = gsrc[i];
+                    if constexpr (PACK) {
+                        s_pro[2 * i] = make_float4(v.x, v.x, v.y, v.y);
+                        s_pro[2 * i + 1] = make_float4(v.z, v.z, v.w, v.w);
+                    } else {
+                        s_pro[i] = v;
+                    }
+                }
                 __syncthreads();
                 staged_chunk = q;
             }
@@ -134,52 +147,136 @@ __global__ void param_kernel(const ParamArgs a)
                 }
                 double* acc_row = s_acc + acc_lig + (size_t)row * a.n_types * 3;
                 const PairG* prow = s_pair + (size_t)row * a.n_types;
-                float aR = 0.f, aH = 0.f, aE = 0.f;
-                int cur = -1;
-                for (int pp = p; pp < pend; ++pp) {
-                    const float4 at = s_pro[pp];
-                    const int tp = __float_as_int(at.w);
-                    if (tp != cur) {  // warp-uniform: every lane reads the same atom
-                        if (cur >= 0) {
-                            const float sR = warp_sum(aR), sH = warp_sum(aH), sE = warp_sum(aE);
-                            if (lane == 0) {
-                                atomicAdd(acc_row + cur * 3 + 0, (double)sR);
-                                atomicAdd(acc_row + cur * 3 + 1, (double)sH);
-                                atomicAdd(acc_row + cur * 3 + 2, (double)sE);
-                            }
-                        }
-                        cur = tp;
-                        aR = 0.f; aH = 0.f; aE = 0.f;
-                    }
-                    const PairG cp = prow[tp];
+                if constexpr (PACK) {
+                    constexpr int H = P / 2;
+                    // ng* accumulate f (p - x') = -dE/dx' per pose, two poses per pair
+                    float2 nx[H], ny[H], nz[H], gx2[H], gy2[H], gz2[H], wv2[H];
 #pragma unroll
-                    for (int k = 0; k < P; ++k) {
-                        const float dx = at.x - xl[k], dy = at.y - yl[k], dz = at.z - zl[k];
-                        const float d2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, kMinD2)));
-                        const float y = rsqrt_approx(d2);
-                        const float d = (V == kFAST) ? d2 * y : sqrt_rn_fma(d2, y);
-                        const float w = clamp01(fmaf(d, -cp.inv_r, 1.f));
-                        const float ve = clamp01(fmaf(d, -(float)(1.0 / kDE), cp.ce));
-                        const float vd = clamp01(fmaf(d, -(float)(1.0 / kDD), cp.cd));
-                        float dedd = cp.hs * w;
-                        dedd = fmaf(ve, fmaf(cp.ae1, ve, cp.ae0), dedd);
-                        dedd = fmaf(vd, fmaf(cp.ad1, vd, cp.ad0), dedd);
-                        const float f = dedd * y;
-                        ngx[k] = fmaf(f, dx, ngx[k]);
-                        ngy[k] = fmaf(f, dy, ngy[k]);
-                        ngz[k] = fmaf(f, dz, ngz[k]);
-                        const float w2 = w * w;
-                        aR = fmaf(wv[k], fmaf(cp.hs, w2, -dedd), aR);
-                        aH = fmaf(wv[k], w2, aH);
-                        aE = fmaf(wv[k], ve * ve * fmaf(-2.f, ve, 3.f), aE);
+                    for (int j = 0; j < H; ++j) {
+                        nx[j] = make_float2(-xl[2 * j], -xl[2 * j + 1]);
+                        ny[j] = make_float2(-yl[2 * j], -yl[2 * j + 1]);
+                        nz[j] = make_float2(-zl[2 * j], -zl[2 * j + 1]);
+                        gx2[j] = gy2[j] = gz2[j] = make_float2(0.f, 0.f);
+                        wv2[j] = make_float2(wv[2 * j], wv[2 * j + 1]);
                     }
-                }
-                if (cur >= 0) {
-                    const float sR = warp_sum(aR), sH = warp_sum(aH), sE = warp_sum(aE);
-                    if (lane == 0) {
-                        atomicAdd(acc_row + cur * 3 + 0, (double)sR);
-                        atomicAdd(acc_row + cur * 3 + 1, (double)sH);
-                        atomicAdd(acc_row + cur * 3 + 2, (double)sE);
+                    const float2 kmin2 = make_float2(kMinD2, kMinD2);
+                    int pp = p;
+                    while (pp < pend) {
+                        const int tp = __float_as_int(s_pro[2 * pp + 1].z);
+                        int run_end = pp + 1;
+                        while (run_end < pend && __float_as_int(s_pro[2 * run_end + 1].z) == tp) ++run_end;
+                        const PairG cp = prow[tp];
+                        const float2 hs2 = make_float2(cp.hs, cp.hs);
+                        const float2 ae1 = make_float2(cp.ae1, cp.ae1), ae0 = make_float2(cp.ae0, cp.ae0);
+                        const float2 ad1 = make_float2(cp.ad1, cp.ad1), ad0 = make_float2(cp.ad0, cp.ad0);
+                        // sums over the run: wv w^2, wv de/dd, wv v_E^2 (3 - 2 v_E); then
+                        // de/dR = hs w^2 - de/dd gives the radius sum as hs sH - sD
+                        float2 aH = make_float2(0.f, 0.f), aD = aH, aE = aH;
+                        auto atom = [&](auto desolv_tag, int q2) {
+                            constexpr bool DESOLV = decltype(desolv_tag)::value;
+                            const float4 a0 = s_pro[2 * q2], a1 = s_pro[2 * q2 + 1];
+                            const float2 px = make_float2(a0.x, a0.y), py = make_float2(a0.z, a0.w);
+                            const float2 pz = make_float2(a1.x, a1.y);
+#pragma unroll
+                            for (int j = 0; j < H; ++j) {
+                                const float2 dx = __fadd2_rn(px, nx[j]);
+                                const float2 dy = __fadd2_rn(py, ny[j]);
+                                const float2 dz = __fadd2_rn(pz, nz[j]);
+                                float2 d2 = __ffma2_rn(dx, dx, kmin2);
+                                d2 = __ffma2_rn(dy, dy, d2);
+                                d2 = __ffma2_rn(dz, dz, d2);
+                                const float2 y = make_float2(rsqrt_approx(d2.x), rsqrt_approx(d2.y));
+                                const float2 d = (V == kFAST) ? __fmul2_rn(d2, y) : sqrt_rn_fma2(d2, y);
+                                const float2 w = make_float2(clamp01(fmaf(d.x, -cp.inv_r, 1.f)),
+                                                             clamp01(fmaf(d.y, -cp.inv_r, 1.f)));
+                                const float2 ve = make_float2(clamp01(fmaf(d.x, -(float)(1.0 / kDE), cp.ce)),
+                                                              clamp01(fmaf(d.y, -(float)(1.0 / kDE), cp.ce)));
+                                float2 dedd = __fmul2_rn(hs2, w);
+                                dedd = __ffma2_rn(ve, __ffma2_rn(ae1, ve, ae0), dedd);
+                                if constexpr (DESOLV) {
+                                    const float2 vd = make_float2(clamp01(fmaf(d.x, -(float)(1.0 / kDD), cp.cd)),
+                                                                  clamp01(fmaf(d.y, -(float)(1.0 / kDD), cp.cd)));
+                                    dedd = __ffma2_rn(vd, __ffma2_rn(ad1, vd, ad0), dedd);
+                                }
+                                const float2 f = __fmul2_rn(dedd, y);
+                                gx2[j] = __ffma2_rn(f, dx, gx2[j]);
+                                gy2[j] = __ffma2_rn(f, dy, gy2[j]);
+                                gz2[j] = __ffma2_rn(f, dz, gz2[j]);
+                                aH = __ffma2_rn(wv2[j], __fmul2_rn(w, w), aH);
+                                aD = __ffma2_rn(wv2[j], dedd, aD);
+                                const float2 t = __ffma2_rn(ve, make_float2(-2.f, -2.f), make_float2(3.f, 3.f));
+                                aE = __ffma2_rn(__fmul2_rn(wv2[j], __fmul2_rn(ve, ve)), t, aE);
+                            }
+                        };
+                        if (cp.ad1 != 0.f || cp.ad0 != 0.f) {
+#pragma unroll 1
+                            for (; pp < run_end; ++pp) atom(std::integral_constant<bool, true>(), pp);
+                        } else {
+#pragma unroll 1
+                            for (; pp < run_end; ++pp) atom(std::integral_constant<bool, false>(), pp);
+                        }
+                        const float sH = warp_sum(aH.x + aH.y), sD = warp_sum(aD.x + aD.y);
+                        const float sE = warp_sum(aE.x + aE.y);
+                        if (lane == 0) {
+                            atomicAdd(acc_row + tp * 3 + 0, (double)cp.hs * (double)sH - (double)sD);
+                            atomicAdd(acc_row + tp * 3 + 1, (double)sH);
+                            atomicAdd(acc_row + tp * 3 + 2, (double)sE);
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < H; ++j) {
+                        ngx[2 * j] = gx2[j].x; ngx[2 * j + 1] = gx2[j].y;
+                        ngy[2 * j] = gy2[j].x; ngy[2 * j + 1] = gy2[j].y;
+                        ngz[2 * j] = gz2[j].x; ngz[2 * j + 1] = gz2[j].y;
+                    }
+                } else {
+                    float aR = 0.f, aH = 0.f, aE = 0.f;
+                    int cur = -1;
+                    for (int pp = p; pp < pend; ++pp) {
+                        const float4 at = s_pro[pp];
+                        const int tp = __float_as_int(at.w);
+                        if (tp != cur) {  // warp-uniform: every lane reads the same atom
+                            if (cur >= 0) {
+                                const float sR = warp_sum(aR), sH = warp_sum(aH), sE = warp_sum(aE);
+                                if (lane == 0) {
+                                    atomicAdd(acc_row + cur * 3 + 0, (double)sR);
+                                    atomicAdd(acc_row + cur * 3 + 1, (double)sH);
+                                    atomicAdd(acc_row + cur * 3 + 2, (double)sE);
+                                }
+                            }
+                            cur = tp;
+                            aR = 0.f; aH = 0.f; aE = 0.f;
+                        }
+                        const PairG cp = prow[tp];
+#pragma unroll
+                        for (int k = 0; k < P; ++k) {
+                            const float dx = at.x - xl[k], dy = at.y - yl[k], dz = at.z - zl[k];
+                            const float d2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, kMinD2)));
+                            const float y = rsqrt_approx(d2);
+                            const float d = (V == kFAST) ? d2 * y : sqrt_rn_fma(d2, y);
+                            const float w = clamp01(fmaf(d, -cp.inv_r, 1.f));
+                            const float ve = clamp01(fmaf(d, -(float)(1.0 / kDE), cp.ce));
+                            const float vd = clamp01(fmaf(d, -(float)(1.0 / kDD), cp.cd));
+                            float dedd = cp.hs * w;
+                            dedd = fmaf(ve, fmaf(cp.ae1, ve, cp.ae0), dedd);
+                            dedd = fmaf(vd, fmaf(cp.ad1, vd, cp.ad0), dedd);
+                            const float f = dedd * y;
+                            ngx[k] = fmaf(f, dx, ngx[k]);
+                            ngy[k] = fmaf(f, dy, ngy[k]);
+                            ngz[k] = fmaf(f, dz, ngz[k]);
+                            const float w2 = w * w;
+                            aR = fmaf(wv[k], fmaf(cp.hs, w2, -dedd), aR);
+                            aH = fmaf(wv[k], w2, aH);
+                            aE = fmaf(wv[k], ve * ve * fmaf(-2.f, ve, 3.f), aE);
+                        }
+                    }
+                    if (cur >= 0) {
+                        const float sR = warp_sum(aR), sH = warp_sum(aH), sE = warp_sum(aE);
+                        if (lane == 0) {
+                            atomicAdd(acc_row + cur * 3 + 0, (double)sR);
+                            atomicAdd(acc_row + cur * 3 + 1, (double)sH);
+                            atomicAdd(acc_row + cur * 3 + 2, (double)sE);
+                        }
                     }
                 }
                 // dL/dx_l += sum_k (w_k/2) R_k^T g_k with g_k = -ng_k
@@ -300,7 +397,7 @@ size_t param_smem_bytes(int P, int n_lig, int n_rows, int n_types, int chunk)
     size_t off = (acc + 15) & ~size_t(15);
     off += 13 * TP * sizeof(float);
     off += (size_t)n_rows * n_types * sizeof(PairG);
-    return off + (size_t)chunk * sizeof(float4);
+    return off + (size_t)chunk * param_atom_bytes(P);
 }
 
 cudaError_t launch_param_reduce(const double* cta_acc, int n_cta, int n_lig, int n_rows,

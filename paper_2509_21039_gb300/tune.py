@@ -90,12 +90,15 @@ def candidates(variant: str, space=None, grad: bool = False, cull: int = 0):
 
 
 def tune_plain(deck, poses, variant: str, space=None, reps: int = 5, grad: bool = False,
-               log=None, cull: int = 0):
-    """Fastest launch shape of bude_energies (or bude_pose_grad) on this input."""
+               log=None, cull: int = 0, param: bool = False):
+    """Fastest launch shape of bude_energies (or bude_pose_grad, or with param
+    bude_param_grad) on this input."""
     out = torch.empty(poses.shape[1], dtype=torch.float32, device=poses.device)
     results = []
-    for o in candidates(variant, space, grad, cull):
-        if grad:
+    for o in candidates(variant, space, grad or param, cull):
+        if param:
+            fn = lambda: bude.param_grad(deck, poses, opts=o)  # noqa: E731
+        elif grad:
             fn = lambda: bude.pose_grad(deck, poses, want_energy=True, opts=o)  # noqa: E731
         else:
             fn = lambda: bude.energies(deck, poses, out=out, opts=o)  # noqa: E731
@@ -171,6 +174,8 @@ def _workloads(which):
         yield "grad", [synth.make_deck(4, **synth.GRAD)]
     if "grad_cull" in which:
         yield "grad_cull", [synth.make_deck(4, **synth.GRAD)]
+    if "param" in which:
+        yield "param", [synth.make_deck(4, **synth.GRAD)]
     if "batched" in which:
         yield "batched", synth.make_batched(3, 64)
 
@@ -217,6 +222,13 @@ def main(argv=None):
                 res = tune_plain(decks[0], poses[0], v, space, a.reps, log=log, cull=1)
                 k = key(v, bucket(len(d["lig_type"]), len(d["pro_type"]), d["poses"].shape[1]),
                         "cull")
+            elif name == "param":
+                if v not in ("fast", "ieee"):
+                    continue
+                d = decks_np[0]
+                res = tune_plain(decks[0], poses[0], v, space, a.reps, log=log, param=True)
+                k = key(v, bucket(len(d["lig_type"]), len(d["pro_type"]), d["poses"].shape[1]),
+                        "param")
             elif name in ("grad", "grad_cull"):
                 if v not in ("fast", "ieee"):
                     continue

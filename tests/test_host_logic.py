@@ -106,11 +106,11 @@ def test_committed_tuned_table_is_well_formed():
     for k, e in t.items():
         gpu, variant, mode, b = k.split("|")
         assert variant in ("fast", "ieee", "comp", "fp64")
-        assert mode in ("plain", "grad", "batched", "cull", "grad_cull")
+        assert mode in ("plain", "grad", "batched", "cull", "grad_cull", "param")
         assert e["ppwi"] in (1, 2, 4, 8, 16)
         assert 64 <= e["block"] <= 1024 and e["block"] % 32 == 0
         assert 1 <= e["ctas_per_sm"] <= 4 and e["ms"] > 0
-        if mode.startswith("grad"):
+        if mode.startswith("grad") or mode == "param":
             assert e["ppwi"] <= 8
         if e.get("cull"):
             assert e["ppwi"] % 2 == 0
