@@ -154,6 +154,22 @@ BUDE_API int bude_energies(bude_deck* deck, const float* poses, int64_t n,
                   float* energies, const bude_options* opts, void* stream);
 
 /*
+ * bude_energies_host -- bude_energies with HOST poses and energies (the
+ * end-to-end call; no paper counterpart).
+ *
+ * poses:    host float32 [6][n] (pinned memory lets the copies overlap).
+ * energies: host float32 [n].
+ * The call copies the poses into a device staging buffer the deck owns,
+ * runs bude_energies on it and copies the energies back, all enqueued on
+ * "stream"; the energies are in host memory once the stream has been
+ * synchronised.  The first call with a larger n than before grows the
+ * staging buffer (synchronising "stream" when it replaces a smaller one).
+ * Same errors as bude_energies.  Calls on one deck must not overlap.
+ */
+BUDE_API int bude_energies_host(bude_deck* deck, const float* poses, int64_t n,
+                                float* energies, const bude_options* opts, void* stream);
+
+/*
  * bude_energies_batched -- many decks in one persistent launch.
  *
  * decks[i], poses[i] (device [6][n[i]]) and energies[i] (device [n[i]]) for

@@ -77,6 +77,7 @@ def load(path: str | None = None):
                                 ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "bude_energies": (ci, [vp, vp, i64, vp, ctypes.POINTER(Options), vp]),
         "bude_energies_noalloc": (ci, [vp, vp, i64, vp, ctypes.POINTER(Options), vp]),
+        "bude_energies_host": (ci, [vp, vp, i64, vp, ctypes.POINTER(Options), vp]),
         "bude_energies_batched": (ci, [ctypes.POINTER(vp), ctypes.POINTER(vp),
                                        ctypes.POINTER(i64), ctypes.POINTER(vp), i32,
                                        ctypes.POINTER(Options), vp]),
@@ -272,6 +273,31 @@ def energies(deck: Deck, poses: torch.Tensor, out: torch.Tensor | None = None,
                               ctypes.c_void_p(out.data_ptr()), ctypes.byref(o),
                               _stream_ptr(stream))
     _check(rc)
+    return out
+
+
+def energies_host(deck: Deck, poses: torch.Tensor, out: torch.Tensor | None = None,
+                  opts=None, stream=None, **kw) -> torch.Tensor:
+    """bude_energies_host: energies of HOST poses (CPU float32 [6][n]; pinned
+    lets the copies overlap) into a host tensor.  The library does both copies
+    on the stream; this returns after synchronising it."""
+    if poses.device.type != "cpu" or poses.dtype != torch.float32 or poses.dim() != 2 \
+            or poses.shape[0] != 6 or not poses.is_contiguous():
+        raise ValueError("poses must be a contiguous CPU float32 [6, n] tensor")
+    n = poses.shape[1]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, pin_memory=poses.is_pinned())
+    if out.device.type != "cpu" or out.shape != (n,) or out.dtype != torch.float32 \
+            or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CPU float32 [n] tensor")
+    o = _opts(opts, **kw)
+    with torch.cuda.device(deck.device):
+        st = stream if stream is not None else torch.cuda.current_stream()
+        rc = load().bude_energies_host(deck.handle, ctypes.c_void_p(poses.data_ptr()), n,
+                                       ctypes.c_void_p(out.data_ptr()), ctypes.byref(o),
+                                       ctypes.c_void_p(st.cuda_stream))
+        _check(rc)
+        st.synchronize()
     return out
 
 

@@ -61,6 +61,9 @@ struct bude_deck {
     size_t partial_bytes = 0;
     unsigned* counter = nullptr;
     size_t counter_count = 0;
+    // staging of bude_energies_host: poses [6][n] then energies [n]
+    float* io = nullptr;
+    size_t io_floats = 0;
 };
 
 namespace {
@@ -680,6 +683,7 @@ int bude_destroy_deck(bude_deck* d)
     cudaFree(d->ff);
     cudaFree(d->partial);
     cudaFree(d->counter);
+    cudaFree(d->io);
     delete d;
     return BUDE_OK;
 }
@@ -700,6 +704,45 @@ int bude_energies(bude_deck* deck, const float* poses, int64_t n, float* energie
 {
     Range range_("bude_energies");
     return run_single(deck, poses, n, energies, nullptr, opts, stream, false);
+}
+
+int bude_energies_host(bude_deck* deck, const float* poses, int64_t n, float* energies,
+                       const bude_options* opts, void* stream)
+{
+    Range range_("bude_energies_host");
+    g_launches = 0;
+    if (!deck) return fail(BUDE_ERR_INVALID_ARG, "deck is NULL");
+    if (n < 0) return fail(BUDE_ERR_INVALID_ARG, "n = %lld < 0", (long long)n);
+    if (n == 0) return BUDE_OK;
+    if (!poses || !energies) return fail(BUDE_ERR_INVALID_ARG, "poses or energies is NULL");
+    int rc, dev;
+    if ((rc = current_device(&dev))) return rc;
+    if (dev != deck->device)
+        return fail(BUDE_ERR_INVALID_ARG, "deck lives on device %d, current device is %d",
+                    deck->device, dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t need = (size_t)n * 7;
+    if (need > deck->io_floats) {
+        if (deck->io) {
+            CK(cudaStreamSynchronize(s), "staging sync");
+            cudaFree(deck->io);
+            deck->io = nullptr;
+            deck->io_floats = 0;
+        }
+        CK(dev_alloc((void**)&deck->io, need * sizeof(float)), "staging allocation");
+        deck->io_floats = need;
+    }
+    float* dp = deck->io;
+    float* de = deck->io + (size_t)n * 6;
+    CK(cudaMemcpyAsync(dp, poses, (size_t)n * 6 * sizeof(float), cudaMemcpyHostToDevice, s),
+       "pose upload");
+    rc = run_single(deck, dp, n, de, nullptr, opts, stream, false);
+    if (rc) return rc;
+    const int64_t launches = g_launches;
+    CK(cudaMemcpyAsync(energies, de, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s),
+       "energy download");
+    g_launches = launches;
+    return BUDE_OK;
 }
 
 int bude_pose_grad(bude_deck* deck, const float* poses, int64_t n, float* energies, float* grad,
