@@ -842,8 +842,13 @@ int bude_energies_batched(bude_deck* const* decks, const float* const* poses, co
         e = cudaGraphInstantiate(&bp->exec, bp->graph, 0);
         if (e) return bail(cuda_fail(e, "graph instantiation"));
         bp->launches = launches;
+        // a plan another thread finished first for the same key wins; ours goes
         std::lock_guard<std::mutex> lk(g_batch_mutex);
-        g_batches[key] = bp;
+        auto ins = g_batches.emplace(key, bp);
+        if (!ins.second) {
+            delete bp;
+            bp = ins.first->second;
+        }
     }
     CK(cudaGraphLaunch(bp->exec, s), "graph launch");
     g_launches = bp->launches;
@@ -1088,7 +1093,11 @@ extern "C" BUDE_API int bude_refine(bude_deck* deck, float* poses, int64_t n, in
         e = cudaGraphInstantiate(&rp->exec, rp->graph, 0);
         if (e) return bail(cuda_fail(e, "graph instantiation"));
         std::lock_guard<std::mutex> lk(g_refine_mutex);
-        g_refines[key] = rp;
+        auto ins = g_refines.emplace(key, rp);
+        if (!ins.second) {
+            delete rp;
+            rp = ins.first->second;
+        }
     }
     CK(cudaGraphLaunch(rp->exec, s), "graph launch");
     g_launches = rp->launches;
