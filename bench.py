@@ -415,6 +415,11 @@ def hartree_fock(bude, synth, dev, timed):
         G64 = hf.fock(D, tol=1e-12, variant="fp64")
         G32 = hf.fock(D, tol=1e-12, variant="ieee")
         row["fp32_vs_fp64_max_rel"] = ((G32 - G64).abs().max() / G64.abs().max()).item()
+        # surviving quartets and primitive integrals per second (ngauss^4 each)
+        q = hf.quartets(1e-12)
+        row["quartets"] = q
+        row["fp32_primitive_integrals_per_s"] = q * 81 / (row["fp32_integrals_ms"] / 1e3)
+        row["fp64_primitive_integrals_per_s"] = q * 81 / (row["fp64_ms"] / 1e3)
         out[f"a={n} ngauss=3"] = row
         hf.close()
     return out

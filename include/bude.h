@@ -333,6 +333,12 @@ BUDE_API int bude_hf_create(int32_t n_atoms, const double* geom, int32_t ngauss,
 BUDE_API int bude_hf_fock(bude_hf* plan, const double* dens, double* g, double schwarz_tol,
                           int32_t variant, void* stream);
 BUDE_API int bude_hf_destroy(bude_hf* plan);
+/*
+ * bude_hf_quartets: the number of unique quartets that survive schwarz_tol,
+ * i.e. how many integrals (each of ngauss^4 primitive quartets) a
+ * bude_hf_fock call with that threshold evaluates.  Synchronises "stream".
+ */
+BUDE_API int bude_hf_quartets(bude_hf* plan, double schwarz_tol, int64_t* count, void* stream);
 
 /* Default options the library uses for a variant when a field is zero. */
 BUDE_API int bude_get_default_options(int32_t variant, bude_options* out);

@@ -88,6 +88,7 @@ def load(path: str | None = None):
         "bude_hf_create": (ci, [i32, vp, i32, vp, vp, vp, ctypes.POINTER(vp)]),
         "bude_hf_fock": (ci, [vp, vp, vp, ctypes.c_double, i32, vp]),
         "bude_hf_destroy": (ci, [vp]),
+        "bude_hf_quartets": (ci, [vp, ctypes.c_double, ctypes.POINTER(i64), vp]),
         "bude_laplacian": (ci, [i32, vp, vp, i32, i32, i32, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_double, vp]),
         "bude_get_default_options": (ci, [i32, ctypes.POINTER(Options)]),
@@ -466,6 +467,12 @@ class HartreeFock:
                                  _stream_ptr(stream))
         _check(rc)
         return out
+
+    def quartets(self, tol: float = 1e-12, stream=None) -> int:
+        """Unique quartets that survive the Schwarz threshold ``tol``."""
+        c = ctypes.c_int64()
+        _check(load().bude_hf_quartets(self._h, float(tol), ctypes.byref(c), _stream_ptr(stream)))
+        return int(c.value)
 
     def close(self):
         if getattr(self, "_h", None) is not None:

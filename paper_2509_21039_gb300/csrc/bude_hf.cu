@@ -462,6 +462,23 @@ extern "C" BUDE_API int bude_hf_create(int32_t n_atoms, const double* geom, int3
     return BUDE_OK;
 }
 
+extern "C" BUDE_API int bude_hf_quartets(bude_hf* h, double tol, int64_t* count, void* stream)
+{
+    Range range_("bude_hf_quartets");
+    if (!h || !count || tol < 0.0 || !std::isfinite(tol)) return BUDE_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long cb = std::max(1ll, std::min<long long>(4096, (h->m + 255) / 256));
+    hf_count_kernel<<<(unsigned)cb, 256, 0, s>>>(h->view(), tol, h->counts);
+    hf_scan_kernel<<<1, 1024, 0, s>>>(h->counts, h->m, h->prefix);
+    long long total = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&total, h->prefix + h->m, sizeof total, cudaMemcpyDeviceToHost, s) ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return BUDE_ERR_CUDA;
+    *count = total;
+    return BUDE_OK;
+}
+
 extern "C" BUDE_API int bude_hf_fock(bude_hf* h, const double* dens, double* g, double tol,
                                      int32_t variant, void* stream)
 {

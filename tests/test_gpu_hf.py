@@ -61,3 +61,25 @@ def test_fock_linear_in_density_and_rejects_bad_input():
         hf.fock(D, variant="fast")
     with pytest.raises(bude.BudeError):
         bude.HartreeFock(s["geom"], -s["xpnt"], s["coef"], device=DEV)
+
+
+def test_surviving_quartet_count_matches_a_host_count():
+    # the work list's size against a plain count over the unique quartets
+    # (IJ >= KL) with the oracle's Schwarz bounds; thresholds a hair apart
+    # bracket any product within rounding of the threshold
+    s = synth.make_he_lattice(12, 20, 3)
+    hf = bude.HartreeFock(s["geom"], s["xpnt"], s["coef"], device=DEV)
+    g, x, c = s["geom"], s["xpnt"], s["coef"]
+    Q = np.array([np.sqrt(abs(oracle.eri(x, c, g[i], g[j], g[i], g[j])))
+                  for i in range(20) for j in range(i + 1)])
+    m = len(Q)
+    prod = Q[:, None] * Q[None, :]
+    iu = np.tril_indices(m)
+    assert hf.quartets(0.0) == m * (m + 1) // 2
+    for tol in (1e-12, 1e-8, 1e-4):
+        lo = int((prod[iu] >= tol * (1 + 1e-9)).sum())
+        hi = int((prod[iu] >= tol * (1 - 1e-9)).sum())
+        assert lo <= hf.quartets(tol) <= hi, tol
+    with pytest.raises(bude.BudeError):
+        hf.quartets(-1.0)
+    hf.close()
