@@ -42,8 +42,8 @@ FP32_LANES_PER_SM = 128
 # profiles/pose_kernel_fast_64x2672x65536_launches.md).  Reported only
 # while the kernel source and the launch shape are the ones that were
 # measured.
-MEASURED_TRAFFIC = {"kernel_sha256_16": "840e310b3fe0b6d3", "variant": "fast", "ppwi": 8,
-                    "block": 512, "bytes": 1842176.0}
+MEASURED_TRAFFIC = {"kernel_sha256_16": "840e310b3fe0b6d3", "variant": "fast", "ppwi": 16,
+                    "block": 384, "bytes": 1892921.0}
 
 # FP32 FLOPs the kernel executes per pose-pair on the full deck, from ncu's
 # per-opcode thread-instruction counters of the same launch (FADD, FMUL 1;

@@ -26,6 +26,15 @@ SPACE = {
     "ctas_per_sm": [1, 2, 3, 4],
     "tile": [0],
 }
+# Protein-tile lengths (atoms staged per shared-memory chunk; 0 = as many as
+# fit) tried in a second stage on the best shapes of the first.
+TILES = [256, 512, 1024, 2048]
+TILE_STAGE_TOP = 3
+
+
+def _with_tile(o, t):
+    return bude.LaunchOptions(variant=o.variant, ppwi=o.ppwi, block=o.block,
+                              ctas_per_sm=o.ctas_per_sm, tile=t, cull=o.cull)
 
 
 def bucket(n_lig: int, n_pro: int, n_poses: int) -> str:
@@ -113,7 +122,31 @@ def tune_plain(deck, poses, variant: str, space=None, reps: int = 5, grad: bool 
             log(f"{variant} P={o.ppwi:2d} block={o.block:4d} cps={o.ctas_per_sm} "
                 f"tile={o.tile} cull={o.cull}: {ms:.3f} ms")
     results.sort(key=lambda r: r[0])
-    return results
+    return _tile_stage(results, fn_of=lambda o: (lambda: (
+        bude.param_grad(deck, poses, opts=o) if param else
+        bude.pose_grad(deck, poses, want_energy=True, opts=o) if grad else
+        bude.energies(deck, poses, out=out, opts=o))), reps=reps, log=log, tag=variant)
+
+
+def _tile_stage(results, fn_of, reps, log, tag):
+    """Second stage: the best shapes again with each protein-tile length."""
+    extra = []
+    for _, o in results[:TILE_STAGE_TOP]:
+        for t in TILES:
+            ot = _with_tile(o, t)
+            try:
+                ms = time_call(fn_of(ot), reps)
+            except bude.BudeError as e:
+                if e.code != bude.ERR_UNSUPPORTED:
+                    raise
+                continue
+            extra.append((ms, ot))
+            if log:
+                log(f"{tag} P={ot.ppwi:2d} block={ot.block:4d} cps={ot.ctas_per_sm} "
+                    f"tile={ot.tile} cull={ot.cull}: {ms:.3f} ms")
+    out = results + extra
+    out.sort(key=lambda r: r[0])
+    return out
 
 
 def tune_batched(decks, poses, variant: str, space=None, reps: int = 5, log=None):
@@ -131,7 +164,8 @@ def tune_batched(decks, poses, variant: str, space=None, reps: int = 5, log=None
             log(f"batched {variant} P={o.ppwi:2d} block={o.block:4d} cps={o.ctas_per_sm}: "
                 f"{ms:.3f} ms")
     results.sort(key=lambda r: r[0])
-    return results
+    return _tile_stage(results, fn_of=lambda o: (lambda: bude.energies_batched(
+        decks, poses, outs, opts=o)), reps=reps, log=log, tag=f"batched {variant}")
 
 
 def record(table: dict, k: str, ms: float, o) -> None:
@@ -243,7 +277,7 @@ def main(argv=None):
                 k = key(v, bucket(len(d["lig_type"]), len(d["pro_type"]), d["poses"].shape[1]))
             if res:
                 record(table, k, res[0][0], res[0][1])
-                top = ", ".join(f"P{o.ppwi}/b{o.block}/c{o.ctas_per_sm}:{ms:.3f}"
+                top = ", ".join(f"P{o.ppwi}/b{o.block}/c{o.ctas_per_sm}/t{o.tile}:{ms:.3f}"
                                 for ms, o in res[:5])
                 print(f"{k}: {top}", flush=True)
         for d in decks:
