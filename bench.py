@@ -229,12 +229,20 @@ def batched_vs_plain(bude, synth, tune, dev, timed, variant="fast", count=64, se
 
     ms_b, lb = timed(run_batched, 10, 3)
     ms_p, lp = timed(run_plain, 10, 3)
-    # the same batched launch with cutoff culling (opt-in; bit-identical)
-    ob_c = bude.LaunchOptions(variant=ob.variant, ppwi=ob.ppwi, block=ob.block,
-                              ctas_per_sm=ob.ctas_per_sm, tile=ob.tile, cull=1)
+    # the batched launch with cutoff culling (opt-in) in the culled kernel's
+    # tuned shape, checked bit for bit against the unculled kernel of that shape
+    oc = tune.lookup(variant, 64, 2672, 65536, mode="cull") or \
+        bude.LaunchOptions(variant=variant, ppwi=8, block=256)
+    ob_c = bude.LaunchOptions(variant=variant, ppwi=oc.ppwi, block=oc.block,
+                              ctas_per_sm=oc.ctas_per_sm, tile=oc.tile, cull=1)
+    ob_u = bude.LaunchOptions(variant=variant, ppwi=oc.ppwi, block=oc.block,
+                              ctas_per_sm=oc.ctas_per_sm, tile=oc.tile, cull=0)
     outs_c = [torch.empty_like(o) for o in outs_b]
+    outs_u = [torch.empty_like(o) for o in outs_b]
     ms_c, _ = timed(lambda: bude.energies_batched(decks, poses, outs_c, opts=ob_c), 10, 3)
-    cull_same = all(bool(torch.equal(a, c)) for a, c in zip(outs_b, outs_c))
+    bude.energies_batched(decks, poses, outs_u, opts=ob_u)
+    torch.cuda.synchronize()
+    cull_same = all(bool(torch.equal(a, c)) for a, c in zip(outs_u, outs_c))
     pairs = sum(len(d["lig_type"]) * len(d["pro_type"]) * d["poses"].shape[1] for d in decks_np)
     n = sum(d["poses"].shape[1] for d in decks_np)
     diff = max(float(((a - b).abs() / b.abs().clamp_min(1.0)).max()) for a, b in zip(outs_b, outs_p))
@@ -248,7 +256,9 @@ def batched_vs_plain(bude, synth, tune, dev, timed, variant="fast", count=64, se
             "batched_launches": lb // 10, "plain_launches": plain_launches[0],
             "batched_opts": {"ppwi": ob.ppwi, "block": ob.block, "ctas_per_sm": ob.ctas_per_sm},
             "max_rel_diff_batched_vs_plain": diff,
-            "batched_cull_ms": statistics.mean(ms_c), "batched_cull_bit_identical": cull_same}
+            "batched_cull_ms": statistics.mean(ms_c), "batched_cull_bit_identical": cull_same,
+            "batched_cull_opts": {"ppwi": ob_c.ppwi, "block": ob_c.block,
+                                  "ctas_per_sm": ob_c.ctas_per_sm}}
 
 
 def adjoint_throughput(bude, synth, tune, dev, timed, variant="fast"):
@@ -323,7 +333,7 @@ def cull_throughput(bude, tune, deck, poses, out, ms_brute, timed, variant="fast
     be bit-identical to the brute-force kernel of the same launch shape."""
     import torch
     o = tune.lookup(variant, 64, 2672, poses.shape[1], mode="cull") or \
-        bude.LaunchOptions(variant=variant, ppwi=16, block=384, cull=1)
+        bude.LaunchOptions(variant=variant, ppwi=8, block=256, cull=1)
     o.cull = 1
     ms, _ = timed(lambda: bude.energies(deck, poses, out=out, opts=o), 20, 3)
     culled = out.clone()

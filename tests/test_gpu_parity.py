@@ -279,10 +279,10 @@ def test_full_size_sampled_against_oracle():
 
 
 def test_flat_work_index_beyond_2_pow_31():
-    # 2^22 poses of the full deck: the flat space (tiles x 64 x 2672 pairs) is
-    # about 2.8e9 iterations, past 32-bit indexing; sampled against the oracle,
-    # the last pose included
-    D = synth.make_deck(9, 64, 2672, 34, 1 << 22)
+    # 2^23 poses of the full deck: the flat space (tiles x 64 x 2672 pairs) is
+    # 2.8e9 iterations or more at any P <= 16, past 32-bit indexing; sampled
+    # against the oracle, the last pose included
+    D = synth.make_deck(9, 64, 2672, 34, 1 << 23)
     deck = bude.Deck(D, device=DEV)
     P = torch.from_numpy(D["poses"]).to(DEV)
     o = _bench_options("fast", 64, 2672, 65536)
