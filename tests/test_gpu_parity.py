@@ -193,6 +193,23 @@ def test_negative_and_zero_hardness(variant, ppwi):
     assert grad_error(G.cpu().numpy(), Gref, S, variant) <= GRAD_GATE[variant]
 
 
+@pytest.mark.parametrize("hb", [(0,), (1, 2), (0, 0), (0, 1), (2, 0, 1)])
+@pytest.mark.parametrize("variant,ppwi,block", [("ieee", 16, 384), ("fast", 8, 512),
+                                                ("comp", 4, 256), ("ieee", 1, 128)])
+def test_degenerate_type_sets(hb, variant, ppwi, block):
+    # one type (a single run per chunk), only polar types (no desolvation term
+    # anywhere, donor-acceptor doubling), only apolar types, and mixtures: the
+    # packed kernels' runs, desolvation skip and row-cost split at their limits
+    nt = len(hb)
+    D = synth.make_deck(170 + nt, 9, 333, nt, 700)
+    D["hbtype"] = np.array(hb, np.int32)
+    D["poses"][3:] *= 0.4
+    check(D, variant, ppwi=ppwi, block=block)
+    E1 = run(D, D["poses"][:, :1].copy(), variant, ppwi=ppwi, block=block)   # one pose
+    ref1, A1 = oracle.energies(D, D["poses"][:, :1], n_threads=-1, with_abs=True)
+    assert scaled_error(E1, ref1, A1).max() <= GATE[variant]
+
+
 def test_type_indexing_is_exact_with_many_types():
     # FP64 on the GPU matches to 1e-12: any wrong type lookup would be gross
     D = synth.make_deck(110, 40, 400, 64, 256)
