@@ -172,7 +172,8 @@ size_t protein_bytes(int variant, int P, bool G) { return packed(variant, P, G) 
 // Per-chunk run table and ligand-row cost prefix of the packed kernels.
 size_t run_bytes(int variant, int P, bool G, int n_types, int n_lig)
 {
-    return packed(variant, P, G) ? run_area_bytes(n_types, n_lig) : 0;
+    // the packed kernels and the FP64 kernel walk same-type runs (mirrors RUNS)
+    return (packed(variant, P, G) || variant == BUDE_FP64) ? run_area_bytes(n_types, n_lig) : 0;
 }
 
 // Dynamic shared memory of pose_kernel before the pair table and protein
