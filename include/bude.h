@@ -297,16 +297,39 @@ BUDE_API int bude_stream(int32_t op, int32_t dtype, void* a, void* b, void* c, d
                          int64_t n, double* dot_result, void* stream);
 
 /*
- * bude_laplacian -- seven-point stencil on an nx x ny x nz grid (index
- * i*ny*nz + j*nz + k, k fastest), interior points only:
+ * bude_laplacian -- seven-point stencil on an nx x ny x nz grid (Sec. 2.2,
+ * Listing 2; bytes by Eq. 1), index i*ny*nz + j*nz + k, k fastest, interior
+ * points only:
  *   f[i,j,k] = u[i,j,k] invhxyz2 + (u[i-1,j,k] + u[i+1,j,k]) invhx2
  *            + (u[i,j-1,k] + u[i,j+1,k]) invhy2 + (u[i,j,k-1] + u[i,j,k+1]) invhz2
  * Boundary points of f are not written.  u and f are distinct device arrays
  * of dtype 0 float32 or 1 float64.  Grids with a side below 3 are a no-op.
+ * Both kernels evaluate the same expression in the same order, so the result
+ * does not depend on which one runs.  BUDE_ERR_UNSUPPORTED: a grid beyond
+ * the launch limits (ny or nx above about 2.6e5).  Asynchronous on "stream".
+ *
+ * bude_laplacian_path -- which kernel bude_laplacian takes for these
+ * arguments (host logic only; u is not dereferenced): 1 the TMA kernel
+ * (float32, u 16-byte aligned, nz a multiple of 4), 0 the register kernel,
+ * or a negative error code for invalid arguments.
+ *
+ * bude_wait_timeouts -- synchronises "stream", then returns in *count, and
+ * clears, the number of CTAs of the TMA stencil whose bounded wait for a
+ * staged plane gave up (about a second) since the last call.  Such a CTA
+ * leaves its tile of f unwritten for the rest of its planes, lets its copies
+ * in flight land, and exits; the CUDA context stays usable.  0 in normal
+ * operation.
+ *
+ * bude_debug_stall_next_stencil -- test hook: the next launch of the TMA
+ * stencil has its first CTA skip the copy of its second computed plane, with
+ * a wait limit of about a millisecond, so that exactly that CTA times out.
  */
 BUDE_API int bude_laplacian(int32_t dtype, const void* u, void* f, int32_t nx, int32_t ny,
                             int32_t nz, double invhx2, double invhy2, double invhz2,
                             double invhxyz2, void* stream);
+BUDE_API int bude_laplacian_path(int32_t dtype, const void* u, int32_t nx, int32_t ny, int32_t nz);
+BUDE_API int bude_wait_timeouts(uint32_t* count, void* stream);
+BUDE_API int bude_debug_stall_next_stencil(void);
 
 /*
  * Hartree-Fock two-electron Fock term over s-type Gaussians (the paper's

@@ -91,6 +91,9 @@ def load(path: str | None = None):
         "bude_hf_quartets": (ci, [vp, ctypes.c_double, ctypes.POINTER(i64), vp]),
         "bude_laplacian": (ci, [i32, vp, vp, i32, i32, i32, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_double, vp]),
+        "bude_laplacian_path": (ci, [i32, vp, i32, i32, i32]),
+        "bude_wait_timeouts": (ci, [ctypes.POINTER(ctypes.c_uint32), vp]),
+        "bude_debug_stall_next_stencil": (ci, []),
         "bude_get_default_options": (ci, [i32, ctypes.POINTER(Options)]),
         "bude_set_default_options": (ci, [ctypes.POINTER(Options)]),
         "bude_last_launch_count": (i64, []),
@@ -434,6 +437,29 @@ def laplacian(u: torch.Tensor, f: torch.Tensor, invhx2=1.0, invhy2=1.0, invhz2=1
                                float(invhy2), float(invhz2), float(invhxyz2), _stream_ptr(stream))
     _check(rc)
     return f
+
+
+def laplacian_path(u: torch.Tensor) -> str:
+    """"tma" or "register": the kernel bude_laplacian takes for u."""
+    if u.dim() != 3:
+        raise ValueError("u: [nx, ny, nz]")
+    rc = load().bude_laplacian_path(_dtype_code(u), ctypes.c_void_p(u.data_ptr()), *u.shape)
+    if rc < 0:
+        _check(rc)
+    return "tma" if rc == 1 else "register"
+
+
+def wait_timeouts(stream=None) -> int:
+    """Synchronise and return (and clear) the count of stencil CTAs whose
+    bounded wait for a staged plane gave up."""
+    n = ctypes.c_uint32(0)
+    _check(load().bude_wait_timeouts(ctypes.byref(n), _stream_ptr(stream)))
+    return int(n.value)
+
+
+def debug_stall_next_stencil() -> None:
+    """Test hook: the next TMA stencil launch has its first CTA time out."""
+    _check(load().bude_debug_stall_next_stencil())
 
 
 class HartreeFock:

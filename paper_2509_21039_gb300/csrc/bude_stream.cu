@@ -5,11 +5,22 @@
 //    over 16-byte vectors with streaming (evict-first) loads and stores, four
 //    vectors in flight per thread; dot reduces per warp with shuffles, per
 //    CTA in shared memory and over CTAs in a fixed order (FP64 partials).
-//  - Seven-point stencil: each thread keeps a column of CH + 2 values along
-//    the slowest index in registers and reads the j/k neighbours through the
-//    read-only path (L1 hits inside the CTA's tile); no barriers, so many
-//    independent loads are in flight.
+//  - Seven-point stencil, FP32: each CTA marches a 128 x 16 (k, j) tile down
+//    a chunk of planes i; TMA tensor copies stage the tile with its halo, one
+//    plane per copy, in a ring of six shared-memory stages, so several planes
+//    are in flight per CTA while the threads compute the current one.  Each
+//    thread keeps the planes i-1, i and i+1 of its own eight points in
+//    registers and reads only the k and j halo from shared memory.
+//  - Seven-point stencil, FP64 (and FP32 arrays a TMA map cannot describe):
+//    each thread keeps a column of CH + 2 values along the slowest index in
+//    registers and reads the j/k neighbours through the read-only path (L1
+//    hits inside the CTA's tile); no barriers, so many independent loads are
+//    in flight.
 #include <algorithm>
+#include <atomic>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "bude_internal.h"
 
@@ -192,6 +203,178 @@ __global__ void __launch_bounds__(TX * TY) laplacian_kernel(const T* __restrict_
     }
 }
 
+// ---- TMA-staged FP32 stencil ----------------------------------------------
+//
+// Output tile: kLapTK columns k x kLapTJ rows j, aligned to the tile size (so
+// every warp's stores cover one aligned 128-byte line); a CTA computes the
+// planes [ia, ib) of its chunk and reads the planes ia-1 .. ib.  A stage holds
+// the box of kLapBJ = TJ + 2 rows x kLapBK = TK + 8 columns whose origin is
+// (max(k0 - 4, 0), max(j0 - 1, 0)): the column origin stays a multiple of four
+// floats (16 bytes, as a tiled TMA copy requires) and never negative; the box
+// reaches past the array on the high side, where the copy fills zeros that
+// only non-interior points read.
+constexpr int kLapTK = 128, kLapTJ = 16, kLapRJ = 8, kLapNS = 6;
+constexpr int kLapBK = kLapTK + 8, kLapBJ = kLapTJ + 2;
+constexpr int kLapStageFloats = ((kLapBK * kLapBJ * 4 + 127) / 128) * 128 / 4;
+constexpr uint32_t kLapBoxBytes = kLapBK * kLapBJ * 4;
+constexpr size_t kLapSmem = 128 + (size_t)kLapNS * kLapStageFloats * 4 + kLapNS * 8;
+
+// CTAs whose wait on a stage gave up (see laplacian_tma_kernel); read and
+// cleared by bude_wait_timeouts.
+static __device__ unsigned g_wait_timeouts;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Wait for the phase of parity "parity" of the mbarrier at "bar" to complete,
+// giving up after "limit" SM clock cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long limit)
+{
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+// One thread (tid 0) issues the copies; stage s holds plane p when
+// (p - (ia - 1)) mod NS = s, and its mbarrier completes one phase per copy.
+// A stage is refilled only after the barrier that ends the step which read
+// it for the last time.  Every wait is bounded: if one gives up, all threads
+// learn it at the step's barrier (__syncthreads_or), stop, and thread 0
+// counts the timeout and waits (bounded again) for every copy it issued that
+// has not landed, so that no copy writes to the CTA's shared memory after
+// it exits.  stall_cta >= 0 makes that CTA skip the copy of plane ia + 1 (a
+// stage that nothing fills), to exercise this path.
+__global__ void __launch_bounds__(kLapTK * (kLapTJ / kLapRJ))
+laplacian_tma_kernel(const __grid_constant__ CUtensorMap tm, float* __restrict__ f, int nx, int ny,
+                     int nz, int chi, float cx, float cy, float cz, float c0, long long limit,
+                     int stall_cta)
+{
+    constexpr int TK = kLapTK, TJ = kLapTJ, RJ = kLapRJ, NS = kLapNS, BK = kLapBK;
+    extern __shared__ unsigned char smem_raw[];
+    float* stage = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
+                                            ~uintptr_t(127));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage + NS * kLapStageFloats);
+
+    const int tid = threadIdx.y * TK + threadIdx.x;
+    const int k0 = blockIdx.x * TK, j0 = blockIdx.y * TJ;
+    const int xs = max(k0 - 4, 0), ys = max(j0 - 1, 0);
+    const int ia = 1 + blockIdx.z * chi;
+    const int ib = min(nx - 1, ia + chi);
+    if (ia >= ib) return;
+    const bool stall =
+        stall_cta >= 0 &&
+        (int)(blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)) == stall_cta;
+    const int k = k0 + threadIdx.x;
+    const int jt = j0 + threadIdx.y * RJ;  // first of this thread's RJ rows
+    const int col = k - xs, row0 = jt - ys;
+    const int left = max(col - 1, 0), up = max(row0 - 1, 0);  // clamped only where k or j is 0
+    const bool kin = k >= 1 && k <= nz - 2;
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[s]))
+                         : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int p) {
+        if (stall && p == ia + 1) return;
+        const int s = (p - (ia - 1)) % NS;
+        const uint32_t bar = smem_addr(&bars[s]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"(kLapBoxBytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(stage + s * kLapStageFloats)),
+            "l"(reinterpret_cast<uint64_t>(&tm)), "r"(xs), "r"(ys), "r"(p), "r"(bar)
+            : "memory");
+    };
+    int issued = ia - 2;  // highest plane issued (thread 0)
+    if (tid == 0)
+        for (int p = ia - 1; p < ia - 1 + NS && p <= ib; ++p) {
+            issue(p);
+            issued = p;
+        }
+    auto wait_plane = [&](int p, bool& good) -> const float* {
+        const int q = p - (ia - 1);
+        if (!mbar_wait_bounded(smem_addr(&bars[q % NS]), (q / NS) & 1, limit)) good = false;
+        return stage + (q % NS) * kLapStageFloats;
+    };
+    float prev[RJ], cur[RJ], nxt[RJ];
+    bool good = true;
+    {
+        const float* P = wait_plane(ia - 1, good);
+#pragma unroll
+        for (int r = 0; r < RJ; ++r) prev[r] = P[(row0 + r) * BK + col];
+        const float* C = wait_plane(ia, good);
+#pragma unroll
+        for (int r = 0; r < RJ; ++r) cur[r] = C[(row0 + r) * BK + col];
+    }
+    bool ok = !__syncthreads_or(!good);
+    if (ok && tid == 0 && ia - 1 + NS <= ib) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(ia - 1 + NS);
+        issued = ia - 1 + NS;
+    }
+    const size_t plane = (size_t)ny * nz;
+    int i = ia;
+    for (; ok && i < ib; ++i) {
+        const float* N = wait_plane(i + 1, good);
+#pragma unroll
+        for (int r = 0; r < RJ; ++r) nxt[r] = N[(row0 + r) * BK + col];
+        const float* C = stage + ((i - (ia - 1)) % NS) * kLapStageFloats;
+        float zl[RJ], zr[RJ];
+#pragma unroll
+        for (int r = 0; r < RJ; ++r) {
+            zl[r] = C[(row0 + r) * BK + left];
+            zr[r] = C[(row0 + r) * BK + col + 1];
+        }
+        const float yu = C[up * BK + col], yd = C[(row0 + RJ) * BK + col];
+        float* fo = f + (size_t)i * plane + (size_t)jt * nz + k;
+#pragma unroll
+        for (int r = 0; r < RJ; ++r) {
+            const float yn = r == 0 ? yu : cur[r - 1];
+            const float yp = r == RJ - 1 ? yd : cur[r + 1];
+            const float v = cur[r] * c0 + (prev[r] + nxt[r]) * cx + (yn + yp) * cy + (zl[r] + zr[r]) * cz;
+            const int j = jt + r;
+            if (good && kin && j >= 1 && j <= ny - 2) fo[(size_t)r * nz] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < RJ; ++r) {
+            prev[r] = cur[r];
+            cur[r] = nxt[r];
+        }
+        ok = !__syncthreads_or(!good);
+        if (ok && tid == 0 && i + NS <= ib) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(i + NS);
+            issued = i + NS;
+        }
+    }
+    if (!ok && tid == 0) {
+        atomicAdd(&g_wait_timeouts, 1u);
+        // A wait that failed in step i (or in the prologue, i = ia) leaves the
+        // planes after i - 1 (ia - 1) possibly in flight: let each land.
+        for (int p = max(ia - 1, i - 1); p <= issued; ++p) {
+            const int q = p - (ia - 1);
+            mbar_wait_bounded(smem_addr(&bars[q % NS]), (q / NS) & 1, limit);
+        }
+    }
+}
+
 // Partial sums of dot: one slot per CTA of the launch, shared by all calls
 // (the library's fixed device array; calls must not overlap on the GPU).
 constexpr int kMaxStreamCtas = 4096;
@@ -238,18 +421,140 @@ cudaError_t stream_launch(int op, T* a, T* b, T* c, T s, long long n, double* do
     return e;
 }
 
+constexpr int kRegTX = 64, kRegTY = 4, kRegCH = 8;
+
+// The register kernel's grid (k tiles, j tiles, plane chunks) within the
+// launch limits (65535 in y and z).
+bool laplacian_reg_fits(int nx, int ny)
+{
+    return (ny - 2 + kRegTY - 1) / kRegTY <= 65535 && (nx - 2 + kRegCH - 1) / kRegCH <= 65535;
+}
+
 template <typename T>
 cudaError_t laplacian_launch(const T* u, T* f, int nx, int ny, int nz, T cx, T cy, T cz, T c0,
                              cudaStream_t st)
 {
-    constexpr int TX = 64, TY = 4, CH = 8;
+    constexpr int TX = kRegTX, TY = kRegTY, CH = kRegCH;
     dim3 grid((unsigned)((nz - 2 + TX - 1) / TX), (unsigned)((ny - 2 + TY - 1) / TY),
               (unsigned)((nx - 2 + CH - 1) / CH));
     laplacian_kernel<T, TX, TY, CH><<<grid, dim3(TX, TY), 0, st>>>(u, f, nx, ny, nz, cx, cy, cz, c0);
     return cudaGetLastError();
 }
 
+// Whether the TMA kernel can stage u: FP32, a 16-byte aligned base and rows
+// of a multiple of 16 bytes (nz % 4 == 0), as the tensor map requires, and a
+// grid within the launch limits.  Host logic only: u is not dereferenced.
+bool laplacian_tma_eligible(int dtype, uintptr_t u, int nx, int ny, int nz)
+{
+    return dtype == 0 && (u & 15u) == 0 && nz % 4 == 0 && nx >= 3 && ny >= 3 && nz >= 4 &&
+           (ny + kLapTJ - 1) / kLapTJ <= 65535;
+}
+
+// Planes per CTA: the chunk length in [8, 128] that best fills whole waves of
+// the resident CTAs, counting the two halo planes each chunk reads again.
+int laplacian_tma_chunk(int nx, int ny, int nz, long long slots)
+{
+    const int interior = nx - 2;
+    const long long tiles = (long long)((nz + kLapTK - 1) / kLapTK) * ((ny + kLapTJ - 1) / kLapTJ);
+    double best = -1.0;
+    int best_c = std::min(interior, 128);
+    for (int c = std::min(interior, 128); c >= std::min(interior, 8); --c) {
+        const long long chunks = (interior + c - 1) / c;
+        if (chunks > 65535) break;
+        const long long items = tiles * chunks;
+        const double waves = (double)((items + slots - 1) / slots);
+        const double eff = (double)items / (waves * (double)slots) * c / (c + 2.0);
+        if (eff > best + 1e-9) {
+            best = eff;
+            best_c = c;
+        }
+    }
+    return best_c;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::atomic<void*> fn{nullptr};
+    void* p = fn.load();
+    if (!p) {
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        fn.store(p);
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+}
+
+std::atomic<int> g_stall_next_stencil{0};
+
+// Launch the TMA kernel; *launched = false (and cudaSuccess) when the tensor
+// map cannot be encoded, so that the caller uses the register kernel.
+cudaError_t laplacian_tma_launch(const float* u, float* f, int nx, int ny, int nz, float cx,
+                                 float cy, float cz, float c0, cudaStream_t st, bool* launched)
+{
+    *launched = false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaSuccess;
+    CUtensorMap tm;
+    cuuint64_t dims[3] = {(cuuint64_t)nz, (cuuint64_t)ny, (cuuint64_t)nx};
+    cuuint64_t strides[2] = {(cuuint64_t)nz * 4, (cuuint64_t)ny * nz * 4};
+    cuuint32_t box[3] = {kLapBK, kLapBJ, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(u), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(laplacian_tma_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLapSmem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int threads = kLapTK * (kLapTJ / kLapRJ);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, laplacian_tma_kernel, threads, kLapSmem);
+    if (e != cudaSuccess) return e;
+    const int chi = laplacian_tma_chunk(nx, ny, nz, (long long)std::max(occ, 1) * sms);
+    dim3 grid((unsigned)((nz + kLapTK - 1) / kLapTK), (unsigned)((ny + kLapTJ - 1) / kLapTJ),
+              (unsigned)((nx - 2 + chi - 1) / chi));
+    // About a second at GB300's clock; a millisecond for the armed stall.
+    const bool stall = g_stall_next_stencil.exchange(0) != 0;
+    const long long limit = stall ? 2000000ll : 2000000000ll;
+    laplacian_tma_kernel<<<grid, dim3(kLapTK, kLapTJ / kLapRJ), kLapSmem, st>>>(
+        tm, f, nx, ny, nz, chi, cx, cy, cz, c0, limit, stall ? 0 : -1);
+    *launched = true;
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+extern "C" BUDE_API int bude_laplacian_path(int32_t dtype, const void* u, int32_t nx, int32_t ny,
+                                            int32_t nz)
+{
+    if ((dtype != 0 && dtype != 1) || nx < 0 || ny < 0 || nz < 0) return BUDE_ERR_INVALID_ARG;
+    return laplacian_tma_eligible(dtype, (uintptr_t)u, nx, ny, nz) ? 1 : 0;
+}
+
+extern "C" BUDE_API int bude_wait_timeouts(uint32_t* count, void* stream)
+{
+    if (!count) return BUDE_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_wait_timeouts) != cudaSuccess) return BUDE_ERR_CUDA;
+    unsigned h = 0;
+    if (cudaMemcpyAsync(&h, p, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemsetAsync(p, 0, sizeof h, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        return BUDE_ERR_CUDA;
+    *count = h;
+    return BUDE_OK;
+}
+
+extern "C" BUDE_API int bude_debug_stall_next_stencil(void)
+{
+    g_stall_next_stencil.store(1);
+    return BUDE_OK;
+}
 
 extern "C" BUDE_API int bude_stream(int32_t op, int32_t dtype, void* a, void* b, void* c,
                                     double scalar, int64_t n, double* dot_result, void* stream)
@@ -287,9 +592,15 @@ extern "C" BUDE_API int bude_laplacian(int32_t dtype, const void* u, void* f, in
     if ((dtype != 0 && dtype != 1) || nx < 0 || ny < 0 || nz < 0) return BUDE_ERR_INVALID_ARG;
     if (nx < 3 || ny < 3 || nz < 3) return BUDE_OK;  // no interior points
     if (!u || !f || u == f) return BUDE_ERR_INVALID_ARG;
-    if ((long long)(ny - 2 + 7) / 8 > 65535 || (long long)(nx - 2 + 7) / 8 > 65535)
-        return BUDE_ERR_UNSUPPORTED;
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
+    bool done = false;
+    if (laplacian_tma_eligible(dtype, (uintptr_t)u, nx, ny, nz))
+        e = laplacian_tma_launch((const float*)u, (float*)f, nx, ny, nz, (float)invhx2,
+                                 (float)invhy2, (float)invhz2, (float)invhxyz2,
+                                 (cudaStream_t)stream, &done);
+    if (e != cudaSuccess) return BUDE_ERR_CUDA;
+    if (done) return BUDE_OK;
+    if (!laplacian_reg_fits(nx, ny)) return BUDE_ERR_UNSUPPORTED;
     if (dtype == 0)
         e = laplacian_launch<float>((const float*)u, (float*)f, nx, ny, nz, (float)invhx2,
                                     (float)invhy2, (float)invhz2, (float)invhxyz2,

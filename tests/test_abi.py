@@ -70,3 +70,20 @@ def test_pack_atoms_keeps_type_bits():
     rec = bude.pack_atoms(np.array([[1.0, 2.0, 3.0]]), np.array([33]))
     assert rec.dtype == np.float32 and rec.shape == (1, 4)
     assert rec[0, 3:].view(np.int32)[0] == 33
+
+
+def test_laplacian_kernel_selection_is_host_logic(lib):
+    # the TMA stencil needs float32, a 16-byte aligned u and rows of a multiple
+    # of 16 bytes; the pointer is only inspected, never dereferenced
+    path = lib.bude_laplacian_path
+    a = ctypes.c_void_p(1 << 20)
+    assert path(0, a, 64, 64, 64) == 1
+    assert path(0, a, 3, 3, 4) == 1
+    assert path(0, ctypes.c_void_p((1 << 20) + 4), 64, 64, 64) == 0   # misaligned base
+    assert path(0, a, 64, 64, 62) == 0                                # rows of 248 bytes
+    assert path(1, a, 64, 64, 64) == 0                                # float64: register kernel
+    assert path(0, a, 2, 64, 64) == 0                                 # no interior
+    assert path(0, a, 64, 64, 3) == 0
+    assert path(2, a, 64, 64, 64) == bude.ERR_INVALID_ARG
+    assert path(0, a, -1, 64, 64) == bude.ERR_INVALID_ARG
+    assert lib.bude_wait_timeouts(None, None) == bude.ERR_INVALID_ARG

@@ -66,6 +66,17 @@ def test_laplacian_of_quadratic_is_exact(dtype):
     assert np.all(F[:, :, -1] == -1)
 
 
+def _stencil_atol(dtype, coef):
+    """Rounding bound of the stencil on u in [0, 1): four operations (three
+    sums and the fused multiply-adds), each off by at most one unit of
+    roundoff of a partial sum no larger than S = |c0| + 2 (|cx| + |cy| + |cz|);
+    twice that for margin.  The result itself may cancel to far below S, so a
+    relative tolerance on it does not apply."""
+    eps = np.finfo(np.float32 if dtype == torch.float32 else np.float64).eps
+    cx, cy, cz, c0 = coef
+    return 8 * eps * (abs(c0) + 2 * (abs(cx) + abs(cy) + abs(cz)))
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 @pytest.mark.parametrize("shape", [(3, 3, 3), (5, 40, 33), (33, 9, 130), (64, 64, 64)])
 def test_laplacian_matches_oracle(dtype, shape):
@@ -76,8 +87,7 @@ def test_laplacian_matches_oracle(dtype, shape):
     ref = so.laplacian(u0.numpy(), *coef, f=f0.numpy())
     f = f0.to(DEV)
     bude.laplacian(u0.to(DEV), f, *coef)
-    tol = 1e-6 if dtype == torch.float32 else 1e-14
-    np.testing.assert_allclose(f.cpu().numpy(), ref, rtol=tol, atol=tol)
+    np.testing.assert_allclose(f.cpu().numpy(), ref, rtol=0, atol=_stencil_atol(dtype, coef))
 
 
 def test_calibration_edge_cases():
@@ -87,3 +97,99 @@ def test_calibration_edge_cases():
         bude.stream_op("copy", a=x[1:5], c=x[:4])        # misaligned start
     u = torch.zeros((2, 5, 5), device=DEV)
     bude.laplacian(u, torch.zeros_like(u))              # no interior: no-op
+
+
+def _misaligned_copy(u):
+    """The same values in a buffer whose base is 4 bytes past a 16-byte
+    boundary, so that bude_laplacian takes the register kernel."""
+    base = torch.empty(u.numel() + 1, dtype=u.dtype, device=u.device)
+    v = base[1:].view(u.shape)
+    v.copy_(u)
+    return v
+
+
+@pytest.mark.parametrize("shape", [(3, 3, 4), (3, 17, 8), (7, 19, 44), (131, 33, 260),
+                                   (40, 300, 132), (20, 1000, 8), (300, 20, 36)])
+def test_tma_stencil_matches_oracle_and_register_kernel(shape):
+    g = torch.Generator().manual_seed(7 + sum(shape))
+    u0 = torch.rand(shape, generator=g, dtype=torch.float32)
+    coef = (0.7, 1.3, 2.1, -8.2)
+    ref = so.laplacian(u0.numpy(), *coef, f=np.full(shape, -3.0, np.float32))
+    u = u0.to(DEV)
+    assert bude.laplacian_path(u) == "tma"
+    f = torch.full(shape, -3.0, device=DEV)
+    bude.laplacian(u, f, *coef)
+    um = _misaligned_copy(u)
+    assert bude.laplacian_path(um) == "register"
+    fr = torch.full(shape, -3.0, device=DEV)
+    bude.laplacian(um, fr, *coef)
+    assert bude.wait_timeouts() == 0
+    # the same expression in the same order: identical bits, boundary untouched
+    assert torch.equal(f, fr)
+    np.testing.assert_allclose(f.cpu().numpy(), ref, rtol=0, atol=_stencil_atol(torch.float32, coef))
+
+
+def test_tma_stencil_quadratic_is_exact():
+    nx, ny, nz = 9, 21, 148
+    i, j, k = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    u = torch.from_numpy((i ** 2 + 2 * j ** 2 + 3 * k ** 2).astype(np.float32)).to(DEV)
+    assert bude.laplacian_path(u) == "tma"
+    f = torch.full_like(u, -1.0)
+    bude.laplacian(u, f, 1.0, 1.0, 1.0, -6.0)
+    F = f.cpu().numpy()
+    assert np.all(F[1:-1, 1:-1, 1:-1] == 12.0)
+    inner = np.zeros(F.shape, bool)
+    inner[1:-1, 1:-1, 1:-1] = True
+    assert np.all(F[~inner] == -1.0)
+
+
+def test_tma_stencil_full_size_sampled():
+    # the bench grid, 1024^3 float32 (4 GiB per array): equal to the register
+    # kernel everywhere, and to the oracle on sampled 4^3 blocks
+    L = 1024
+    g = torch.Generator(device=DEV).manual_seed(11)
+    u = torch.rand((L, L, L), generator=g, device=DEV)
+    f = torch.zeros_like(u)
+    bude.laplacian(u, f)
+    assert bude.laplacian_path(u) == "tma"
+    rng = np.random.default_rng(3)
+    for _ in range(24):
+        i0, j0, k0 = (int(x) for x in rng.integers(1, L - 5, 3))
+        blk = u[i0 - 1:i0 + 5, j0 - 1:j0 + 5, k0 - 1:k0 + 5].cpu().numpy()
+        ref = so.laplacian(blk, 1.0, 1.0, 1.0, -6.0, f=np.zeros_like(blk))[1:-1, 1:-1, 1:-1]
+        got = f[i0:i0 + 4, j0:j0 + 4, k0:k0 + 4].cpu().numpy()
+        np.testing.assert_allclose(got, ref, rtol=0, atol=_stencil_atol(torch.float32, (1, 1, 1, -6)))
+    um = _misaligned_copy(u)
+    del u
+    fr = torch.zeros_like(f)
+    bude.laplacian(um, fr)
+    assert torch.equal(f, fr)
+    assert bude.wait_timeouts() == 0
+
+
+def test_tma_stencil_bounded_wait_gives_up_and_recovers():
+    # a CTA whose staged plane never arrives (its copy is skipped) gives up
+    # after its wait limit, leaves its tile unwritten, and the context and the
+    # next call are unaffected
+    shape = (40, 40, 256)
+    g = torch.Generator().manual_seed(5)
+    u0 = torch.rand(shape, generator=g, dtype=torch.float32)
+    ref = so.laplacian(u0.numpy(), 1.0, 1.0, 1.0, -6.0, f=np.full(shape, -5.0, np.float32))
+    u = u0.to(DEV)
+    assert bude.wait_timeouts() == 0
+    f = torch.full(shape, -5.0, device=DEV)
+    bude.debug_stall_next_stencil()
+    bude.laplacian(u, f)
+    assert bude.wait_timeouts() == 1
+    F = f.cpu().numpy()
+    tol = _stencil_atol(torch.float32, (1, 1, 1, -6))
+    bad = ~np.isclose(F, ref, rtol=0, atol=tol)
+    assert bad.any()
+    assert np.all(F[bad] == -5.0)                       # unwritten, not wrong
+    ii, jj, kk = np.nonzero(bad)
+    assert jj.max() < 16 and kk.max() < 128 and ii.min() == 1   # inside the first CTA's tile
+    assert bad[1, 1:16, 1:128].all()
+    f2 = torch.full(shape, -5.0, device=DEV)
+    bude.laplacian(u, f2)
+    assert bude.wait_timeouts() == 0
+    np.testing.assert_allclose(f2.cpu().numpy(), ref, rtol=0, atol=tol)
