@@ -378,7 +378,7 @@ def param_grad_throughput(bude, synth, tune, dev, timed, variant="fast"):
             "opts": {"ppwi": o.ppwi, "block": o.block, "ctas_per_sm": o.ctas_per_sm}}
 
 
-def hbm_calibration(bude, dev, timed, peak_gbs):
+def hbm_calibration(bude, dev, timed, peak_gbs, stencil_l=1024, stream_sizes=(1 << 25, 1 << 28)):
     """The paper's memory-bound kernels on this GPU: GB/s by Eq. 2 (BabelStream,
     2^25 and 2^28 elements) and Eq. 1 (seven-point stencil, FP32 L=1024, FP64
     L=512), against the measured copy bandwidth."""
@@ -386,7 +386,7 @@ def hbm_calibration(bude, dev, timed, peak_gbs):
     out = {}
     for dtype, name in ((torch.float32, "f32"), (torch.float64, "f64")):
         item = torch.tensor([], dtype=dtype).element_size()
-        for n in (1 << 25, 1 << 28):
+        for n in stream_sizes:
             a = torch.full((n,), 0.1, dtype=dtype, device=dev)
             b = torch.full((n,), 0.2, dtype=dtype, device=dev)
             c = torch.zeros(n, dtype=dtype, device=dev)
@@ -402,7 +402,8 @@ def hbm_calibration(bude, dev, timed, peak_gbs):
                 out[f"{op}_{name}_2^{n.bit_length() - 1}"] = {
                     "gb_s": gbs, "frac_of_measured_copy": gbs / peak_gbs}
             del a, b, c
-        L = 1024 if name == "f32" else 512
+            torch.cuda.empty_cache()
+        L = stencil_l if name == "f32" else stencil_l // 2
         u = torch.rand((L, L, L), dtype=dtype, device=dev)
         f = torch.zeros_like(u)
         ms, _ = timed(lambda: bude.laplacian(u, f, 1.0, 1.0, 1.0, -6.0), 10, 3)
@@ -499,6 +500,10 @@ def main():
     ap.add_argument("--small", action="store_true", help="26x938x4096 deck")
     ap.add_argument("--poses", type=int, default=0, help="override the pose count (profiling)")
     ap.add_argument("--flush-mb", type=int, default=256, help="L2 flush buffer, MiB")
+    ap.add_argument("--hbm-only", action="store_true",
+                    help="only the memory-bound calibration kernels (profiling)")
+    ap.add_argument("--stencil-l", type=int, default=1024,
+                    help="FP32 stencil grid side with --hbm-only (FP64: half)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -559,6 +564,14 @@ def main():
         barrier()
         ms = [a.elapsed_time(b) for a, b in evs]
         return ms, launches
+
+    if args.hbm_only:
+        # profiling entry: the stencil at the given size, BabelStream at 2^25 only
+        res = hbm_calibration(bude, dev, timed, measured_peaks().get("hbm_gbs", 6800.0),
+                              stencil_l=args.stencil_l, stream_sizes=(1 << 25,))
+        if rank == 0:
+            print(json.dumps({"hbm_calibration": res}), flush=True)
+        return
 
     with ClockSampler(local, os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None) as clk:
