@@ -4,7 +4,8 @@
 //  - BabelStream copy / mul / add / triad / dot: persistent grid-stride loops
 //    over 16-byte vectors with streaming (evict-first) loads and stores, four
 //    vectors in flight per thread; dot reduces per warp with shuffles, per
-//    CTA in shared memory and over CTAs in a fixed order (FP64 partials).
+//    CTA in shared memory and over CTAs in a fixed order (FP64 partials),
+//    summed by the last CTA to finish, in the same launch.
 //  - Seven-point stencil, FP32: each CTA marches a 128 x 16 (k, j) tile down
 //    a chunk of planes i; TMA tensor copies stage the tile with its halo, one
 //    plane per copy, in a ring of six shared-memory stages, so several planes
@@ -75,10 +76,16 @@ template <> struct DotAcc<double> { typedef DotAcc64 A; };
 enum StreamOp { kCopy = 0, kMul = 1, kAdd = 2, kTriad = 3, kDot = 4 };
 constexpr int kUnroll = 4;
 
-// One element-wise op over nv vectors (vector part) plus a scalar tail.
+// Tickets of the dot's last-CTA finish (reset by the CTA that takes the last).
+static __device__ unsigned g_dot_ticket;
+
+// One element-wise op over nv vectors (vector part) plus a scalar tail.  dot:
+// each CTA stores its partial sum; the CTA that takes the last ticket sums
+// the partials in a fixed order (so the result does not depend on which CTA
+// finishes last) and writes *dot_out.  Nothing waits.
 template <typename T, int OP>
 __global__ void stream_kernel(T* __restrict__ a, T* __restrict__ b, T* __restrict__ c, T s,
-                              long long n, double* __restrict__ partial)
+                              long long n, double* __restrict__ partial, double* __restrict__ dot_out)
 {
     typedef typename Vec<T>::V V;
     constexpr int NV = Vec<T>::N;
@@ -131,33 +138,34 @@ __global__ void stream_kernel(T* __restrict__ a, T* __restrict__ b, T* __restric
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
         __syncthreads();
+        __shared__ bool s_last;
         if (threadIdx.x == 0) {
             double v = 0.0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_w[w];
             partial[blockIdx.x] = v;
+            __threadfence();
+            s_last = atomicAdd(&g_dot_ticket, 1u) == gridDim.x - 1;
         }
-    }
-}
-
-// Sum of the per-CTA partials by one CTA of 1024 threads: each thread adds
-// the partials i = tid, tid + 1024, ... in order, then a butterfly per warp
-// and the 32 warp sums in warp order.  The order is fixed, so the result is
-// deterministic; a serial loop here cost tens of microseconds at 2^25.
-__global__ void __launch_bounds__(1024) dot_finish_kernel(const double* __restrict__ partial, int n,
-                                                          double* __restrict__ out)
-{
-    __shared__ double s_w[32];
-    double v = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v += partial[i];
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            // thread t adds the partials t, t + blockDim, ... in order (read
+            // through L2: other SMs wrote them), then a butterfly per warp and
+            // the warp sums in warp order
+            double v = 0.0;
+            for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += __ldcg(partial + i);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double w = threadIdx.x < (blockDim.x >> 5) ? s_w[threadIdx.x] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        if (threadIdx.x == 0) *out = w;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            __syncthreads();   // s_w is reused
+            if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double w = 0.0;
+                for (int k = 0; k < (int)(blockDim.x >> 5); ++k) w += s_w[k];
+                *dot_out = w;
+                g_dot_ticket = 0u;
+            }
+        }
     }
 }
 
@@ -404,21 +412,16 @@ cudaError_t stream_launch(int op, T* a, T* b, T* c, T s, long long n, double* do
         if (e != cudaSuccess) return e;
         partial = static_cast<double*>(p);
     }
+    double* o = dot_out;
     switch (op) {
-    case kCopy: stream_kernel<T, kCopy><<<(unsigned)grid, threads, 0, st>>>(a, b, c, s, n, partial); break;
-    case kMul: stream_kernel<T, kMul><<<(unsigned)grid, threads, 0, st>>>(a, b, c, s, n, partial); break;
-    case kAdd: stream_kernel<T, kAdd><<<(unsigned)grid, threads, 0, st>>>(a, b, c, s, n, partial); break;
-    case kTriad: stream_kernel<T, kTriad><<<(unsigned)grid, threads, 0, st>>>(a, b, c, s, n, partial); break;
-    case kDot: stream_kernel<T, kDot><<<(unsigned)grid, threads, 0, st>>>(a, b, c, s, n, partial); break;
+    case kCopy: stream_kernel<T, kCopy><<<(unsigned)grid, threads, 0, st>>>(a, b, c, s, n, partial, o); break;
+    case kMul: stream_kernel<T, kMul><<<(unsigned)grid, threads, 0, st>>>(a, b, c, s, n, partial, o); break;
+    case kAdd: stream_kernel<T, kAdd><<<(unsigned)grid, threads, 0, st>>>(a, b, c, s, n, partial, o); break;
+    case kTriad: stream_kernel<T, kTriad><<<(unsigned)grid, threads, 0, st>>>(a, b, c, s, n, partial, o); break;
+    case kDot: stream_kernel<T, kDot><<<(unsigned)grid, threads, 0, st>>>(a, b, c, s, n, partial, o); break;
     }
-    cudaError_t e = cudaGetLastError();
     *launches = 1;
-    if (e == cudaSuccess && op == kDot) {
-        dot_finish_kernel<<<1, 1024, 0, st>>>(partial, (int)grid, dot_out);
-        e = cudaGetLastError();
-        *launches = 2;
-    }
-    return e;
+    return cudaGetLastError();
 }
 
 constexpr int kRegTX = 64, kRegTY = 4, kRegCH = 8;
