@@ -55,6 +55,7 @@ struct HfPlanDev {
     const double* rkp;
     const float4* rpqf;
     const float* rkpf;
+    const int2* rpairs;     // [m] (i, j) of the pair of each rank
 };
 
 __device__ __forceinline__ void pair_of(long long ij, int* i, int* j)
@@ -143,11 +144,38 @@ __device__ __forceinline__ T contracted(const T4* __restrict__ A, const T4* __re
 }
 
 // The same over the rank-ordered copies: primitive pair ab of rank a is at
-// [ab * m + a].
-template <typename T, typename T4>
+// [ab * m + a].  G2 > 0: that many primitive pairs, known at compile time,
+// with the partner's G2 products loaded up front (all in flight at once) and
+// kept in registers across the loop over ab; G2 = 0: g2 at run time.
+template <typename T, typename T4, int G2>
 __device__ __forceinline__ T contracted_ranked(const T4* __restrict__ pq, const T* __restrict__ kp,
                                                long long m, long long a, long long b, int g2)
 {
+    if constexpr (G2 > 0) {
+        T4 c[G2];
+        T kc[G2];
+#pragma unroll
+        for (int cd = 0; cd < G2; ++cd) {
+            c[cd] = pq[cd * m + b];
+            kc[cd] = kp[cd * m + b];
+        }
+        T v = 0;
+#pragma unroll
+        for (int ab = 0; ab < G2; ++ab) {
+            const T4 x = pq[ab * m + a];
+            const T ka = kp[ab * m + a];
+            T w = 0;
+#pragma unroll
+            for (int cd = 0; cd < G2; ++cd) {
+                const T dx = x.x - c[cd].x, dy = x.y - c[cd].y, dz = x.z - c[cd].z;
+                const T r2 = hf_fma(dz, dz, hf_fma(dy, dy, dx * dx));
+                const T rs = hf_rsqrt(x.w + c[cd].w);   // sqrt(rho)
+                w = hf_fma(kc[cd] * rs, erf_over_x(r2 * rs * rs), w);
+            }
+            v = hf_fma(ka, w, v);
+        }
+        return v;
+    }
     T v = 0;
     for (int ab = 0; ab < g2; ++ab) {
         const T4 x = pq[ab * m + a];
@@ -180,6 +208,14 @@ __global__ void hf_rank_copy_kernel(const HfPlanDev P, double4_32a* __restrict__
         rpqf[e] = P.pqf[src];
         rkpf[e] = P.kpf[src];
     }
+}
+
+// (i, j) of the pair of every rank, once per plan.
+__global__ void hf_rank_pairs_kernel(const HfPlanDev P, int2* __restrict__ rpairs)
+{
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < P.m;
+         a += (long long)gridDim.x * blockDim.x)
+        rpairs[a] = P.pairs[P.order[a]];
 }
 
 __device__ double contracted_f64(const HfPlanDev& P, long long ij, long long kl)
@@ -257,34 +293,51 @@ __global__ void __launch_bounds__(1024) hf_scan_kernel(const long long* __restri
 }
 
 // One thread per surviving quartet: work item x lies in the rank a with
-// prefix[a] <= x < prefix[a + 1] and pairs with rank b = x - prefix[a].
-template <bool F32>
-__global__ void hf_fock_kernel(const HfPlanDev P, const long long* __restrict__ prefix,
-                               const double* __restrict__ D, double* __restrict__ F)
+// prefix[a] <= x < prefix[a + 1] and pairs with rank b = x - prefix[a].  Each
+// warp takes a contiguous range of about total / warps items, its lanes the
+// items x = x0 + lane, x0 + lane + 32, ...: a lane finds its first rank by
+// binary search and every later one by stepping forward from the last (the
+// next item is 32 further on, mostly in the same or the next rank), instead
+// of one search of about log2(m) dependent loads per item.  Consecutive
+// lanes then mostly share the rank a, whose data are warp-uniform loads, and
+// hold consecutive ranks b, whose data are adjacent words.
+template <bool F32, int G2>
+__global__ void __launch_bounds__(128) hf_fock_kernel(const HfPlanDev P,
+                                                      const long long* __restrict__ prefix,
+                                                      const double* __restrict__ D,
+                                                      double* __restrict__ F)
 {
     const long long total = prefix[P.m];
     const int n = P.n;
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
-         x += (long long)gridDim.x * blockDim.x) {
-        long long lo = 0, hi = P.m - 1;  // largest a with prefix[a] <= x
-        while (lo < hi) {
-            const long long mid = (lo + hi + 1) >> 1;
-            if (prefix[mid] <= x) lo = mid; else hi = mid - 1;
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long warp = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long per = ((total + warps - 1) / warps + 31) & ~31ll;
+    const long long x0 = warp * per, x1 = min(total, x0 + per);
+    const int g2 = P.ng * P.ng;
+    long long a = -1;
+    for (long long x = x0 + lane; x < x1; x += 32) {
+        if (a < 0) {
+            long long lo = 0, hi = P.m - 1;  // largest a with prefix[a] <= x
+            while (lo < hi) {
+                const long long mid = (lo + hi + 1) >> 1;
+                if (prefix[mid] <= x) lo = mid; else hi = mid - 1;
+            }
+            a = lo;
+        } else {
+            while (prefix[a + 1] <= x) ++a;
         }
-        const long long a = lo, b = x - prefix[a];
-        const long long IJ = P.order[a], KL = P.order[b];
-        const int2 pij = P.pairs[IJ], pkl = P.pairs[KL];
+        const long long b = x - prefix[a];
+        const int2 pij = P.rpairs[a], pkl = P.rpairs[b];
         const int i = pij.x, j = pij.y, k = pkl.x, l = pkl.y;
-        const int g2 = P.ng * P.ng;
-        double v = F32 ? (double)contracted_ranked<float, float4>(P.rpqf, P.rkpf, P.m, a, b, g2)
-                       : contracted_ranked<double, double4_32a>(P.rpq, P.rkp, P.m, a, b, g2);
+        double v = F32 ? (double)contracted_ranked<float, float4, G2>(P.rpqf, P.rkpf, P.m, a, b, g2)
+                       : contracted_ranked<double, double4_32a, G2>(P.rpq, P.rkp, P.m, a, b, g2);
         if (i == j) v *= 0.5;
         if (k == l) v *= 0.5;
         if (a == b) v *= 0.5;
         // the six updates are symmetric under (ij) <-> (kl) once G = F + F^T.
-        // Consecutive work items mostly share the rank a, so a full warp on one
-        // (ij) adds its F_ij terms in registers first: 32 atomics on one
-        // address would serialise.
+        // A full warp on one (ij) adds its F_ij terms in registers first: 32
+        // atomics on one address would serialise.
         const double cij = 4.0 * D[(size_t)k * n + l] * v;
         const unsigned act = __activemask();
         const long long a0 = __shfl_sync(act, a, 0);
@@ -292,7 +345,7 @@ __global__ void hf_fock_kernel(const HfPlanDev P, const long long* __restrict__ 
             double t = cij;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if ((threadIdx.x & 31) == 0) atomicAdd(F + (size_t)i * n + j, t);
+            if (lane == 0) atomicAdd(F + (size_t)i * n + j, t);
         } else {
             atomicAdd(F + (size_t)i * n + j, cij);
         }
@@ -301,6 +354,31 @@ __global__ void hf_fock_kernel(const HfPlanDev P, const long long* __restrict__ 
         atomicAdd(F + (size_t)i * n + l, -D[(size_t)j * n + k] * v);
         atomicAdd(F + (size_t)j * n + k, -D[(size_t)i * n + l] * v);
         atomicAdd(F + (size_t)j * n + l, -D[(size_t)i * n + k] * v);
+    }
+}
+
+// One wave of CTAs, as many as are resident: the warps' item ranges are
+// equal, so a second, partial wave would only add a tail.
+template <bool F32, int G2>
+cudaError_t launch_fock_g(const HfPlanDev& P, const long long* prefix, const double* D, double* F,
+                          int sms, cudaStream_t s)
+{
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hf_fock_kernel<F32, G2>, 128, 0);
+    if (e != cudaSuccess) return e;
+    hf_fock_kernel<F32, G2><<<(unsigned)(sms * std::max(occ, 1)), 128, 0, s>>>(P, prefix, D, F);
+    return cudaGetLastError();
+}
+
+template <bool F32>
+cudaError_t launch_fock(const HfPlanDev& P, const long long* prefix, const double* D, double* F,
+                        int sms, cudaStream_t s)
+{
+    switch (P.ng) {
+    case 1: return launch_fock_g<F32, 1>(P, prefix, D, F, sms, s);
+    case 2: return launch_fock_g<F32, 4>(P, prefix, D, F, sms, s);
+    case 3: return launch_fock_g<F32, 9>(P, prefix, D, F, sms, s);
+    default: return launch_fock_g<F32, 0>(P, prefix, D, F, sms, s);
     }
 }
 
@@ -339,6 +417,7 @@ struct bude_hf {
     double* rkp = nullptr;
     float4* rpqf = nullptr;
     float* rkpf = nullptr;
+    int2* rpairs = nullptr;      // [m]
     HfPlanDev view() const
     {
         HfPlanDev v;
@@ -357,6 +436,7 @@ struct bude_hf {
         v.rkp = rkp;
         v.rpqf = rpqf;
         v.rkpf = rkpf;
+        v.rpairs = rpairs;
         return v;
     }
 };
@@ -383,6 +463,7 @@ extern "C" BUDE_API int bude_hf_destroy(bude_hf* h)
     cudaFree(h->rkp);
     cudaFree(h->rpqf);
     cudaFree(h->rkpf);
+    cudaFree(h->rpairs);
     delete h;
     return BUDE_OK;
 }
@@ -425,7 +506,8 @@ extern "C" BUDE_API int bude_hf_create(int32_t n_atoms, const double* geom, int3
         dev_alloc((void**)&h->rpq, e * sizeof(double4_32a)) ||
         dev_alloc((void**)&h->rkp, e * sizeof(double)) ||
         dev_alloc((void**)&h->rpqf, e * sizeof(float4)) ||
-        dev_alloc((void**)&h->rkpf, e * sizeof(float)))
+        dev_alloc((void**)&h->rkpf, e * sizeof(float)) ||
+        dev_alloc((void**)&h->rpairs, (size_t)h->m * sizeof(int2)))
         return bail(BUDE_ERR_OOM);
     // host inputs: copied synchronously (plan creation is not on the hot path)
     if (cudaMemcpy(h->geom, geom, 3 * sizeof(double) * n_atoms, cudaMemcpyHostToDevice) ||
@@ -456,6 +538,7 @@ extern "C" BUDE_API int bude_hf_create(int32_t n_atoms, const double* geom, int3
     }
     hf_rank_copy_kernel<<<(unsigned)std::max(1ll, blocks), 256, 0, s>>>(h->view(), h->rpq, h->rkp,
                                                                         h->rpqf, h->rkpf);
+    hf_rank_pairs_kernel<<<(unsigned)std::max(1ll, sb), 128, 0, s>>>(h->view(), h->rpairs);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
         return bail(BUDE_ERR_CUDA);
     *out = h;
@@ -495,11 +578,10 @@ extern "C" BUDE_API int bude_hf_fock(bude_hf* h, const double* dens, double* g, 
     const long long cb = std::max(1ll, std::min<long long>(4096, (h->m + 255) / 256));
     hf_count_kernel<<<(unsigned)cb, 256, 0, s>>>(h->view(), tol, h->counts);
     hf_scan_kernel<<<1, 1024, 0, s>>>(h->counts, h->m, h->prefix);
-    const unsigned blocks = (unsigned)sms * 16;
-    if (variant == BUDE_FP64)
-        hf_fock_kernel<false><<<blocks, 128, 0, s>>>(h->view(), h->prefix, dens, h->fock);
-    else
-        hf_fock_kernel<true><<<blocks, 128, 0, s>>>(h->view(), h->prefix, dens, h->fock);
+    const cudaError_t le = variant == BUDE_FP64
+                               ? launch_fock<false>(h->view(), h->prefix, dens, h->fock, sms, s)
+                               : launch_fock<true>(h->view(), h->prefix, dens, h->fock, sms, s);
+    if (le != cudaSuccess) return BUDE_ERR_CUDA;
     const long long sb = std::max(1ll, std::min<long long>(4096, ((long long)nn + 255) / 256));
     hf_symmetrise_kernel<<<(unsigned)sb, 256, 0, s>>>(h->fock, g, h->n);
     return cudaGetLastError() == cudaSuccess ? BUDE_OK : BUDE_ERR_CUDA;

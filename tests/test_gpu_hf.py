@@ -21,7 +21,7 @@ def _lib():
     bude.load()
 
 
-@pytest.mark.parametrize("n,ng", [(1, 3), (2, 1), (5, 3), (9, 2), (14, 3)])
+@pytest.mark.parametrize("n,ng", [(1, 3), (2, 1), (5, 3), (9, 2), (14, 3), (6, 4), (4, 8)])
 @pytest.mark.parametrize("variant", ["fp64", "ieee"])
 def test_fock_matches_oracle(n, ng, variant):
     s = synth.make_he_lattice(n, n, ng)
