@@ -417,21 +417,25 @@ def hbm_calibration(bude, dev, timed, peak_gbs, stencil_l=1024, stream_sizes=(1 
     return out
 
 
-def hartree_fock(bude, synth, dev, timed):
+def hartree_fock(bude, synth, dev, timed, sizes=(64, 128, 256), variants=("ieee", "fp64")):
     """Two-electron Fock build for synthetic helium lattices of 64, 128 and 256
     atoms with 3 primitives per atom (the paper's Table 4 sizes), FP32
     integrals with FP64 accumulation and all-FP64, Schwarz threshold 1e-12."""
     import torch
     out = {}
-    for n in (64, 128, 256):
+    for n in sizes:
         s = synth.make_he_lattice(11, n, 3)
         hf = bude.HartreeFock(s["geom"], s["xpnt"], s["coef"], device=dev)
         D = torch.from_numpy(s["dens"]).to(dev)
         row = {}
-        for v in ("ieee", "fp64"):
+        for v in variants:
             reps = 1 if (v == "fp64" and n == 256) else 5
             ms, _ = timed(lambda: hf.fock(D, tol=1e-12, variant=v), reps, 1)
             row["fp32_integrals_ms" if v == "ieee" else "fp64_ms"] = statistics.median(ms)
+        if len(variants) < 2:
+            out[f"a={n} ngauss=3"] = row
+            hf.close()
+            continue
         G64 = hf.fock(D, tol=1e-12, variant="fp64")
         G32 = hf.fock(D, tol=1e-12, variant="ieee")
         row["fp32_vs_fp64_max_rel"] = ((G32 - G64).abs().max() / G64.abs().max()).item()
@@ -504,6 +508,8 @@ def main():
                     help="only the memory-bound calibration kernels (profiling)")
     ap.add_argument("--stencil-l", type=int, default=1024,
                     help="FP32 stencil grid side with --hbm-only (FP64: half)")
+    ap.add_argument("--hf-only", type=int, default=0, metavar="ATOMS",
+                    help="only the FP32-integral Fock build on this many atoms (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -564,6 +570,12 @@ def main():
         barrier()
         ms = [a.elapsed_time(b) for a, b in evs]
         return ms, launches
+
+    if args.hf_only:
+        res = hartree_fock(bude, synth, dev, timed, sizes=(args.hf_only,), variants=("ieee",))
+        if rank == 0:
+            print(json.dumps({"hartree_fock": res}), flush=True)
+        return
 
     if args.hbm_only:
         # profiling entry: the stencil at the given size, BabelStream at 2^25 only

@@ -146,7 +146,8 @@ __device__ __forceinline__ T contracted(const T4* __restrict__ A, const T4* __re
 // The same over the rank-ordered copies: primitive pair ab of rank a is at
 // [ab * m + a].  G2 > 0: that many primitive pairs, known at compile time,
 // with the partner's G2 products loaded up front (all in flight at once) and
-// kept in registers across the loop over ab; G2 = 0: g2 at run time.
+// kept in registers across the loop over ab, whose body is unrolled over cd;
+// G2 = 0: g2 at run time.
 template <typename T, typename T4, int G2>
 __device__ __forceinline__ T contracted_ranked(const T4* __restrict__ pq, const T* __restrict__ kp,
                                                long long m, long long a, long long b, int g2)
@@ -160,7 +161,10 @@ __device__ __forceinline__ T contracted_ranked(const T4* __restrict__ pq, const 
             kc[cd] = kp[cd * m + b];
         }
         T v = 0;
-#pragma unroll
+        // the loop over ab stays rolled: unrolled, its G2^2 inlined erf
+        // evaluations overflowed the instruction cache (ncu: warps stalled on
+        // instruction fetch more than on anything else)
+#pragma unroll 1
         for (int ab = 0; ab < G2; ++ab) {
             const T4 x = pq[ab * m + a];
             const T ka = kp[ab * m + a];
