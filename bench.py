@@ -412,6 +412,13 @@ def hbm_calibration(bude, dev, timed, peak_gbs, stencil_l=1024, stream_sizes=(1 
         gbs = (fetch + write) * item / (statistics.median(ms) / 1e3) / 1e9
         out[f"stencil_{name}_L{L}"] = {"gb_s": gbs, "frac_of_measured_copy": gbs / peak_gbs,
                                         "ms": statistics.median(ms)}
+        if name == "f64":
+            # 7 FP64 instructions per interior point (3 sums, 1 product, 3 FMAs)
+            # against GB300's nominal FP64 rate of 1.25 TFLOP/s, i.e. 6.25e11
+            # FMA instructions/s: the bound of this kernel on this GPU
+            ips = 7.0 * (L - 2) ** 3 / (statistics.median(ms) / 1e3)
+            out[f"stencil_{name}_L{L}"].update({
+                "fp64_instructions_per_s": ips, "frac_of_nominal_fp64_rate": ips / 6.25e11})
         del u, f
         torch.cuda.empty_cache()
     return out
