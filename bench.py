@@ -511,6 +511,8 @@ def main():
     ap.add_argument("--small", action="store_true", help="26x938x4096 deck")
     ap.add_argument("--poses", type=int, default=0, help="override the pose count (profiling)")
     ap.add_argument("--flush-mb", type=int, default=256, help="L2 flush buffer, MiB")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="also write the clock samples of the timed region to this CSV file")
     ap.add_argument("--hbm-only", action="store_true",
                     help="only the memory-bound calibration kernels (profiling)")
     ap.add_argument("--stencil-l", type=int, default=1024,
@@ -592,8 +594,7 @@ def main():
             print(json.dumps({"hbm_calibration": res}), flush=True)
         return
 
-    with ClockSampler(local, os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
-                      if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None) as clk:
+    with ClockSampler(local, args.clocks_csv) as clk:
         ms, launches = timed(step, args.steps, args.warmup)
     ms_mean = bdist.max_over_ranks(statistics.mean(ms), dev)
     value = bdist.aggregate_rate(n, ms_mean, world)
