@@ -202,6 +202,13 @@ def _workloads(which):
         yield "small", [synth.make_deck(0, **synth.SMALL)]
     if "full" in which:
         yield "full", [synth.make_deck(1, **synth.FULL)]
+    if "full_fp64" in which:
+        # FP64 is ~100x slower than FP32 on GB300: its shape for the full deck is
+        # tuned on the deck's first 4096 poses (the persistent kernel's choice
+        # depends on the pair loop, not on the pose count once the grid is full)
+        d = synth.make_deck(1, **synth.FULL)
+        d["poses"] = d["poses"][:, :4096].copy()
+        yield "full_fp64", [d]
     if "cull" in which:
         yield "cull", [synth.make_deck(1, **synth.FULL)]
     if "grad" in which:
@@ -216,6 +223,7 @@ def _workloads(which):
 
 def main(argv=None):
     import argparse
+    from . import synth
     ap = argparse.ArgumentParser(description="tune launch shapes and write tuned.json")
     ap.add_argument("--workloads", default="small,full,grad,batched")
     ap.add_argument("--variants", default="fast,ieee,comp,fp64")
@@ -239,10 +247,12 @@ def main(argv=None):
         for v in variants:
             space = None
             if v == "fp64":
-                if name != "small":
-                    continue   # FP64 runs ~60x slower: tune it on the small deck only
-                space = {"ppwi": [1, 2, 4], "block": [128, 256, 512], "ctas_per_sm": [1, 2],
-                         "tile": [0]}
+                if name not in ("small", "full_fp64"):
+                    continue   # FP64 runs ~100x slower: the small deck and 4096 full-deck poses
+                space = {"ppwi": [1, 2, 4], "block": [128, 192, 256, 384, 512],
+                         "ctas_per_sm": [1, 2, 3], "tile": [0]}
+            elif name == "full_fp64":
+                continue
             if name == "batched":
                 if v not in ("fast", "ieee"):
                     continue
@@ -274,7 +284,8 @@ def main(argv=None):
             else:
                 d = decks_np[0]
                 res = tune_plain(decks[0], poses[0], v, space, a.reps, log=log)
-                k = key(v, bucket(len(d["lig_type"]), len(d["pro_type"]), d["poses"].shape[1]))
+                n_poses = synth.FULL["n_poses"] if name == "full_fp64" else d["poses"].shape[1]
+                k = key(v, bucket(len(d["lig_type"]), len(d["pro_type"]), n_poses))
             if res:
                 record(table, k, res[0][0], res[0][1])
                 top = ", ".join(f"P{o.ppwi}/b{o.block}/c{o.ctas_per_sm}/t{o.tile}:{ms:.3f}"
