@@ -1,11 +1,13 @@
 // The paper's memory-bound kernels (arxiv 2509.21039, Sec. 2.2, Listings 2
 // and 3; metrics Eq. 1 and Eq. 2), written for GB300 as HBM calibration
 // beside the compute-bound pose kernel:
-//  - BabelStream copy / mul / add / triad / dot: persistent grid-stride loops
-//    over 16-byte vectors with streaming (evict-first) loads and stores, four
-//    vectors in flight per thread; dot reduces per warp with shuffles, per
-//    CTA in shared memory and over CTAs in a fixed order (FP64 partials),
-//    summed by the last CTA to finish, in the same launch.
+//  - BabelStream copy / mul / add / triad / dot over 16-byte vectors with
+//    streaming (evict-first) loads and stores: the element-wise ops give each
+//    CTA one contiguous chunk (four vectors per thread), dot runs a persistent
+//    grid-stride loop (eight float4 or four double2 in flight) and reduces
+//    per warp with shuffles, per CTA in shared memory and over CTAs in a fixed
+//    order (FP64 partials), summed by the last CTA to finish, in the same
+//    launch.
 //  - Seven-point stencil, FP32: each CTA marches a 128 x 16 (k, j) tile down
 //    a chunk of planes i; TMA tensor copies stage the tile with its halo, one
 //    plane per copy, in a ring of six shared-memory stages, so several planes
@@ -74,14 +76,26 @@ template <typename T> struct DotAcc { typedef DotAcc32 A; };
 template <> struct DotAcc<double> { typedef DotAcc64 A; };
 
 enum StreamOp { kCopy = 0, kMul = 1, kAdd = 2, kTriad = 3, kDot = 4 };
-constexpr int kUnroll = 4;
+// Vectors per thread: element-wise ops take one CTA-sized chunk of 4 per
+// thread and CTA (a grid of as many CTAs as chunks); dot keeps a persistent
+// grid (its per-CTA partials are summed in a fixed order) with 8 float4 or 4
+// double2 in flight (8 lengthened the FP64 accumulator's dependent chain:
+// 0.80 -> 0.69 of the copy bandwidth at 2^25).
+constexpr int kUnrollFlat = 4;
+template <typename T> constexpr int kUnrollDot = 8;
+template <> constexpr int kUnrollDot<double> = 4;
 
 // Tickets of the dot's last-CTA finish (reset by the CTA that takes the last).
 static __device__ unsigned g_dot_ticket;
 
-// One element-wise op over nv vectors (vector part) plus a scalar tail.  dot:
-// each CTA stores its partial sum; the CTA that takes the last ticket sums
-// the partials in a fixed order (so the result does not depend on which CTA
+// One element-wise op over nv vectors (vector part) plus a scalar tail.
+// Element-wise ops: CTA k handles the chunk of blockDim * kUnrollFlat vectors
+// starting at k * that (and every gridDim-th chunk after it, when the grid is
+// capped), its threads one vector per blockDim step, so each CTA reads and
+// writes contiguous memory; at 2^25 floats this beat a persistent
+// grid-stride loop by 8 %.  dot: a persistent grid-stride loop; each CTA
+// stores its partial sum and the CTA that takes the last ticket sums the
+// partials in a fixed order (so the result does not depend on which CTA
 // finishes last) and writes *dot_out.  Nothing waits.
 template <typename T, int OP>
 __global__ void stream_kernel(T* __restrict__ a, T* __restrict__ b, T* __restrict__ c, T s,
@@ -93,34 +107,55 @@ __global__ void stream_kernel(T* __restrict__ a, T* __restrict__ b, T* __restric
     V* av = reinterpret_cast<V*>(a);
     V* bv = reinterpret_cast<V*>(b);
     V* cv = reinterpret_cast<V*>(c);
+    auto one = [&](long long j) {
+        if (OP == kCopy) __stcs(cv + j, __ldcs(av + j));
+        if (OP == kMul) __stcs(bv + j, vmul(s, __ldcs(cv + j)));
+        if (OP == kAdd) __stcs(cv + j, vadd(__ldcs(av + j), __ldcs(bv + j)));
+        if (OP == kTriad) __stcs(av + j, vfma(s, __ldcs(cv + j), __ldcs(bv + j)));
+    };
     const long long stride = (long long)gridDim.x * blockDim.x;
     typename DotAcc<T>::A acc;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    for (; i + (kUnroll - 1) * stride < nv; i += kUnroll * stride) {
-        V x[kUnroll], y[kUnroll];
+    if constexpr (OP != kDot) {
+        constexpr int U = kUnrollFlat;
+        const long long B = blockDim.x, chunk = B * U;
+        for (long long c0 = (long long)blockIdx.x * chunk; c0 < nv; c0 += (long long)gridDim.x * chunk) {
+            const long long end = min(nv, c0 + chunk);
+            const long long i = c0 + threadIdx.x;
+            if (i + (U - 1) * B < end) {
+                V x[U], y[U];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const long long j = i + u * stride;
-            if (OP == kCopy || OP == kAdd || OP == kDot) x[u] = __ldcs(av + j);
-            if (OP == kMul || OP == kTriad) x[u] = __ldcs(cv + j);
-            if (OP == kAdd || OP == kTriad || OP == kDot) y[u] = __ldcs(bv + j);
-        }
+                for (int u = 0; u < U; ++u) {
+                    const long long j = i + u * B;
+                    if (OP == kCopy || OP == kAdd) x[u] = __ldcs(av + j);
+                    if (OP == kMul || OP == kTriad) x[u] = __ldcs(cv + j);
+                    if (OP == kAdd || OP == kTriad) y[u] = __ldcs(bv + j);
+                }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const long long j = i + u * stride;
-            if (OP == kCopy) __stcs(cv + j, x[u]);
-            if (OP == kMul) __stcs(bv + j, vmul(s, x[u]));
-            if (OP == kAdd) __stcs(cv + j, vadd(x[u], y[u]));
-            if (OP == kTriad) __stcs(av + j, vfma(s, x[u], y[u]));
-            if (OP == kDot) vdot(acc, x[u], y[u]);
+                for (int u = 0; u < U; ++u) {
+                    const long long j = i + u * B;
+                    if (OP == kCopy) __stcs(cv + j, x[u]);
+                    if (OP == kMul) __stcs(bv + j, vmul(s, x[u]));
+                    if (OP == kAdd) __stcs(cv + j, vadd(x[u], y[u]));
+                    if (OP == kTriad) __stcs(av + j, vfma(s, x[u], y[u]));
+                }
+            } else {
+                for (long long j = i; j < end; j += B) one(j);
+            }
         }
-    }
-    for (; i < nv; i += stride) {
-        if (OP == kCopy) __stcs(cv + i, __ldcs(av + i));
-        if (OP == kMul) __stcs(bv + i, vmul(s, __ldcs(cv + i)));
-        if (OP == kAdd) __stcs(cv + i, vadd(__ldcs(av + i), __ldcs(bv + i)));
-        if (OP == kTriad) __stcs(av + i, vfma(s, __ldcs(cv + i), __ldcs(bv + i)));
-        if (OP == kDot) vdot(acc, __ldcs(av + i), __ldcs(bv + i));
+    } else {
+        constexpr int U = kUnrollDot<T>;
+        long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        for (; i + (U - 1) * stride < nv; i += U * stride) {
+            V x[U], y[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                x[u] = __ldcs(av + i + u * stride);
+                y[u] = __ldcs(bv + i + u * stride);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) vdot(acc, x[u], y[u]);
+        }
+        for (; i < nv; i += stride) vdot(acc, __ldcs(av + i), __ldcs(bv + i));
     }
     // scalar tail (n not a multiple of the vector width)
     const long long t0 = nv * NV;
@@ -402,9 +437,17 @@ cudaError_t stream_launch(int op, T* a, T* b, T* c, T s, long long n, double* do
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int threads = 256;
-    long long want = (n / Vec<T>::N + threads * kUnroll - 1) / (threads * kUnroll);
-    long long grid = std::max(1ll, std::min<long long>(want, (long long)sms * 8));
-    grid = std::min<long long>(grid, kMaxStreamCtas);
+    const long long nv = n / Vec<T>::N;
+    long long grid;
+    if (op == kDot) {
+        const long long want = (nv + threads * kUnrollDot<T> - 1) / (threads * kUnrollDot<T>);
+        grid = std::min<long long>(std::max(1ll, std::min<long long>(want, (long long)sms * 8)),
+                                   kMaxStreamCtas);
+    } else {
+        // one CTA per chunk; beyond the launch limit the CTAs take several
+        const long long chunks = (nv + threads * kUnrollFlat - 1) / (threads * kUnrollFlat);
+        grid = std::min<long long>(std::max(1ll, chunks), 0x7fffffffll);
+    }
     double* partial = nullptr;
     if (op == kDot) {
         void* p = nullptr;
