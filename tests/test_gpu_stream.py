@@ -52,6 +52,21 @@ def test_dot_is_exact_on_small_integers():
     assert bude.stream_op("dot", a=a, b=b).item() == 2.0 * float((np.arange(n) % 7).sum())
 
 
+def test_stream_ops_beyond_the_cta_cap():
+    # 2^29 floats: 2^17 one-chunk CTAs for the element-wise ops, and a dot
+    # whose grid-stride loop runs many rounds; exact results by construction
+    n = (1 << 29) + 12345
+    a = (torch.arange(n, device=DEV, dtype=torch.int64) % 7).to(torch.float32)
+    b = torch.full((n,), 2.0, device=DEV)
+    expect = 2.0 * ((n // 7) * 21 + sum(range(n % 7)))
+    assert bude.stream_op("dot", a=a, b=b).item() == expect
+    c = torch.empty_like(a)
+    bude.stream_op("copy", a=a, c=c)
+    assert torch.equal(c, a)
+    bude.stream_op("triad", a=c, b=b, c=a, scalar=3.0)   # c = b + 3 a
+    assert torch.equal(c, b + 3.0 * a)
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 def test_laplacian_of_quadratic_is_exact(dtype):
     nx, ny, nz = 7, 19, 45          # ragged tiles in j and k
