@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(1024) hf_scan_kernel(const long long* __restri
 // lanes then mostly share the rank a, whose data are warp-uniform loads, and
 // hold consecutive ranks b, whose data are adjacent words.
 template <bool F32, int G2>
-__global__ void __launch_bounds__(128) hf_fock_kernel(const HfPlanDev P,
+__global__ void __launch_bounds__(128, 1) hf_fock_kernel(const HfPlanDev P,
                                                       const long long* __restrict__ prefix,
                                                       const double* __restrict__ D,
                                                       double* __restrict__ F)
@@ -361,8 +361,12 @@ __global__ void __launch_bounds__(128) hf_fock_kernel(const HfPlanDev P,
     }
 }
 
-// One wave of CTAs, as many as are resident: the warps' item ranges are
-// equal, so a second, partial wave would only add a tail.
+// Two full waves of CTAs: the warps' item ranges are equal, and halving
+// them shortens the end of the launch, where some warps of a CTA are done
+// (measured at 256 atoms: one wave 5.31 ms, two 5.18 ms).  The kernel is
+// built for one CTA per SM at least, which leaves the compiler its register
+// choice (120 registers, 4 CTAs per SM): capping it at 64-80 registers for
+// 6-8 CTAs per SM ran at 6.0-6.6 ms.
 template <bool F32, int G2>
 cudaError_t launch_fock_g(const HfPlanDev& P, const long long* prefix, const double* D, double* F,
                           int sms, cudaStream_t s)
@@ -370,7 +374,7 @@ cudaError_t launch_fock_g(const HfPlanDev& P, const long long* prefix, const dou
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hf_fock_kernel<F32, G2>, 128, 0);
     if (e != cudaSuccess) return e;
-    hf_fock_kernel<F32, G2><<<(unsigned)(sms * std::max(occ, 1)), 128, 0, s>>>(P, prefix, D, F);
+    hf_fock_kernel<F32, G2><<<(unsigned)(2 * sms * std::max(occ, 1)), 128, 0, s>>>(P, prefix, D, F);
     return cudaGetLastError();
 }
 
