@@ -517,6 +517,8 @@ def main():
                     help="only the memory-bound calibration kernels (profiling)")
     ap.add_argument("--stencil-l", type=int, default=1024,
                     help="FP32 stencil grid side with --hbm-only (FP64: half)")
+    ap.add_argument("--stream-log2", default="25",
+                    help="BabelStream sizes with --hbm-only, as log2 of the element count")
     ap.add_argument("--hf-only", type=int, default=0, metavar="ATOMS",
                     help="only the FP32-integral Fock build on this many atoms (profiling)")
     args = ap.parse_args()
@@ -587,9 +589,10 @@ def main():
         return
 
     if args.hbm_only:
-        # profiling entry: the stencil at the given size, BabelStream at 2^25 only
+        # profiling entry: the stencil and BabelStream at the given sizes
+        sizes = tuple(1 << int(x) for x in args.stream_log2.split(","))
         res = hbm_calibration(bude, dev, timed, measured_peaks().get("hbm_gbs", 6800.0),
-                              stencil_l=args.stencil_l, stream_sizes=(1 << 25,))
+                              stencil_l=args.stencil_l, stream_sizes=sizes)
         if rank == 0:
             print(json.dumps({"hbm_calibration": res}), flush=True)
         return
