@@ -1,13 +1,16 @@
 """Multi-process helpers: one process per GPU, no collective on the data path.
 
 Poses are independent and so are decks, so the path shards without any
-exchange: a rank either docks its own deck (weak scaling, what the benchmark
-does) or a contiguous slice of one deck's poses.  The only collectives are
-the benchmark's barrier and the max-over-ranks of its step time; they work
-on any torch.distributed backend (NCCL on GPUs, gloo on CPU).
+exchange: a rank docks its own deck (weak scaling, what the benchmark does),
+a contiguous slice of one deck's poses, or, for a batch of uneven decks, the
+decks that a longest-processing-time-first assignment by pair count gives it.
+The only collectives are the benchmark's barrier and the max-over-ranks of
+its step time; they work on any torch.distributed backend (NCCL on GPUs,
+gloo on CPU).
 """
 from __future__ import annotations
 
+import math
 import os
 
 import torch
@@ -50,3 +53,50 @@ def aggregate_rate(units_per_rank: float, ms_per_step_max: float, world_size: in
     if ms_per_step_max <= 0:
         raise ValueError("step time must be positive")
     return world_size * units_per_rank / (ms_per_step_max / 1e3)
+
+
+def deck_cost(n_lig: int, n_pro: int, n_poses: int) -> int:
+    """Work of one deck: its ligand x protein x pose pair evaluations."""
+    return int(n_lig) * int(n_pro) * int(n_poses)
+
+
+def lpt_partition(costs, world_size: int) -> list[list[int]]:
+    """Indices of the items (decks) each rank takes: longest processing time
+    first, each item in turn (largest cost first, ties by index) to the rank
+    with the least load so far (ties by rank).  Deterministic, so every rank
+    computes the same assignment without an exchange; its largest load is at
+    most (4/3 - 1/(3 world_size)) of the best possible (Graham, 1969)."""
+    if world_size < 1:
+        raise ValueError("world_size must be positive")
+    costs = [float(c) for c in costs]
+    if any(c < 0 for c in costs):
+        raise ValueError("costs must be non-negative")
+    loads = [0.0] * world_size
+    parts: list[list[int]] = [[] for _ in range(world_size)]
+    for i in sorted(range(len(costs)), key=lambda k: (-costs[k], k)):
+        r = min(range(world_size), key=lambda q: (loads[q], q))
+        parts[r].append(i)
+        loads[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
+def split_and_partition(shapes, world_size: int) -> list[list[tuple[int, int, int]]]:
+    """Work of each rank for a batch of uneven decks, as (deck, lo, hi) pose
+    slices.  A deck whose pair count exceeds the per-rank average is cut into
+    that many contiguous pose slices (rounded up, sizes within one pose of
+    each other), so no single piece dominates a rank; the pieces then go to
+    the ranks by lpt_partition.  shapes: (n_lig, n_pro, n_poses) per deck."""
+    if world_size < 1:
+        raise ValueError("world_size must be positive")
+    costs = [deck_cost(*s) for s in shapes]
+    avg = sum(costs) / world_size if costs else 0.0
+    pieces: list[tuple[int, int, int]] = []
+    piece_cost: list[float] = []
+    for d, ((nl, npro, npo), c) in enumerate(zip(shapes, costs)):
+        k = min(int(npo), math.ceil(c / avg)) if avg > 0 and c > avg else 1
+        for r in range(k):
+            lo, hi = shard_range(int(npo), r, k)
+            pieces.append((d, lo, hi))
+            piece_cost.append(float(deck_cost(nl, npro, hi - lo)))
+    parts = lpt_partition(piece_cost, world_size)
+    return [[pieces[i] for i in p] for p in parts]
