@@ -59,21 +59,29 @@ MEASURED_EXECUTED = {"kernel_sha256_16": "19f29abd5002d932",
 MEASURED_EXECUTED_ADJOINT = {"kernel_sha256_16": "19f29abd5002d932", "variant": "fast", "ppwi": 8,
                              "flop_per_pair": 36.77}
 
+# The same count for the FAST forcefield-gradient kernel (param_kernel) at
+# P = 8 on the 64 x 2672 x 16384 workload; the hash covers both of its
+# source files.
+MEASURED_EXECUTED_PARAM = {"kernel_sha256_16": "35ee3b55c9eaf157", "variant": "fast", "ppwi": 8,
+                           "flop_per_pair": 39.12}
 
-def kernel_sha():
-    """First 16 hex digits of the sha256 of the kernel source with comments and
-    whitespace removed, so that edits to comments keep the measurements."""
+
+def kernel_sha(files=("bude_kernels.cuh",)):
+    """First 16 hex digits of the sha256 of the kernel sources (csrc/) with
+    comments and whitespace removed, so that edits to comments keep the
+    measurements."""
     import hashlib
     import re
-    src = os.path.join(ROOT, "paper_2509_21039_gb300", "csrc", "bude_kernels.cuh")
-    try:
-        text = open(src).read()
-    except OSError:
-        return None
-    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
-    text = re.sub(r"//[^\n]*", " ", text)
-    text = " ".join(text.split())
-    return hashlib.sha256(text.encode()).hexdigest()[:16]
+    texts = []
+    for name in files:
+        try:
+            text = open(os.path.join(ROOT, "paper_2509_21039_gb300", "csrc", name)).read()
+        except OSError:
+            return None
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        texts.append(" ".join(text.split()))
+    return hashlib.sha256("\n".join(texts).encode()).hexdigest()[:16]
 
 
 def measured_executed(variant):
@@ -385,9 +393,20 @@ def param_grad_throughput(bude, synth, tune, dev, timed, variant="fast"):
     ms, launches = timed(lambda: bude.param_grad(deck, P, opts=o), 5, 2)
     deck.close()
     t = statistics.mean(ms)
+    m = MEASURED_EXECUTED_PARAM
+    executed = None
+    if (kernel_sha(("bude_kernels.cuh", "bude_param.cu")), variant, o.ppwi) == \
+            (m["kernel_sha256_16"], m["variant"], m["ppwi"]):
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        tf = m["flop_per_pair"] * 64 * 2672 * P.shape[1] / (t / 1e3) / 1e12
+        executed = {"flop_per_pair": m["flop_per_pair"], "tflops": tf, "frac_fp32_peak": tf / peak,
+                    "source": "ncu opcode counters of param_kernel; time of the whole call "
+                              "(three kernels)"}
     return {"workload": "dL/d(ligand xyz, radius, hardness, elsc), L = sum of 16384 pose "
                         "energies, 64 lig x 2672 pro, seed 4",
             "variant": variant, "ms": t, "poses_per_s": P.shape[1] / (t / 1e3),
+            "executed": executed,
             "kernels_per_call": launches // 5,
             "opts": {"ppwi": o.ppwi, "block": o.block, "ctas_per_sm": o.ctas_per_sm}}
 
@@ -533,6 +552,8 @@ def main():
                     help="FP32 stencil grid side with --hbm-only (FP64: half)")
     ap.add_argument("--stream-log2", default="25",
                     help="BabelStream sizes with --hbm-only, as log2 of the element count")
+    ap.add_argument("--param-only", action="store_true",
+                    help="only the forcefield-gradient extra (profiling)")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the pose-gradient (adjoint) extra (profiling)")
     ap.add_argument("--hf-only", type=int, default=0, metavar="ATOMS",
@@ -597,6 +618,12 @@ def main():
         barrier()
         ms = [a.elapsed_time(b) for a, b in evs]
         return ms, launches
+
+    if args.param_only:
+        res = param_grad_throughput(bude, synth, tune, dev, timed, variant=args.variant)
+        if rank == 0:
+            print(json.dumps({"param_grad": res}), flush=True)
+        return
 
     if args.adjoint_only:
         res = adjoint_throughput(bude, synth, tune, dev, timed, variant=args.variant)

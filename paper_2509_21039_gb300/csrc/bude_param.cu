@@ -311,61 +311,91 @@ __global__ void param_kernel(const ParamArgs a)
 }
 
 // Adds the CTAs' accumulators in CTA order: sums[i] = sum_c cta_acc[c][i].
+// The loads of eight CTAs are issued before their sums (same order of
+// additions), so that they are in flight together.
 __global__ void param_sum_kernel(const double* __restrict__ cta_acc, int n_cta, int acc_len,
                                  double* __restrict__ sums)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < acc_len; i += gridDim.x * blockDim.x) {
         double v = 0.0;
-        for (int c = 0; c < n_cta; ++c) v += cta_acc[(size_t)c * acc_len + i];
+        int c = 0;
+        for (; c + 8 <= n_cta; c += 8) {
+            double t[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t[u] = cta_acc[(size_t)(c + u) * acc_len + i];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v += t[u];
+        }
+        for (; c < n_cta; ++c) v += cta_acc[(size_t)c * acc_len + i];
         sums[i] = v;
     }
 }
 
-// Chain rule from the (row, protein type) sums to per-type gradients, one
-// thread per output, each summing its contributions in a fixed order.
-__global__ void param_finish_kernel(const double* __restrict__ sums, int n_lig, int n_rows,
-                                    int n_types, const int* __restrict__ row_type,
-                                    const float4* __restrict__ ff, float* __restrict__ lig_grad,
-                                    float* __restrict__ ff_grad)
+// Chain rule from the (row, protein type) sums to per-type gradients: one
+// CTA per type t (the last CTA copies the ligand gradients).  The CTA's
+// threads split the (row, protein type) pairs in which t takes part, each
+// summing its share in order, and the shares are added in a fixed order (a
+// butterfly per warp, then the warps in order), so the result does not vary
+// from call to call.  (One thread per type walking every pair in turn took
+// 0.37 ms on the 64-atom deck: a chain of dependent loads.)
+__global__ void __launch_bounds__(256) param_finish_kernel(
+    const double* __restrict__ sums, int n_lig, int n_rows, int n_types,
+    const int* __restrict__ row_type, const float4* __restrict__ ff, float* __restrict__ lig_grad,
+    float* __restrict__ ff_grad)
 {
     const int acc_lig = n_lig * 3;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < acc_lig + n_types;
-         i += gridDim.x * blockDim.x) {
-        if (i < acc_lig) {
-            lig_grad[i] = (float)sums[i];
-            continue;
+    const int t = blockIdx.x;
+    if (t >= n_types) {
+        for (int i = threadIdx.x; i < acc_lig; i += blockDim.x) lig_grad[i] = (float)sums[i];
+        return;
+    }
+    double gr = 0.0, gh = 0.0, gq = 0.0;
+    const int pairs = n_rows * n_types;
+    for (int p = threadIdx.x; p < pairs; p += blockDim.x) {
+        const int r = p / n_types, b = p - r * n_types;
+        const int ta = row_type[r];
+        const bool as_a = (ta == t), as_b = (b == t);
+        if (!as_a && !as_b) continue;
+        const double* v = sums + acc_lig + (size_t)p * 3;
+        const float4 fa = ff[ta], fb = ff[b];
+        const int ha = __float_as_int(fa.w), hb = __float_as_int(fb.w);
+        const double wab = ((ha == 1 && hb == 2) || (ha == 2 && hb == 1)) ? 2.0 : 1.0;
+        const double v0 = v[0], v1 = v[1], v2 = v[2];
+        if (as_a) {
+            gr += v0;
+            gh += 0.5 * v1;
+            gq += kKE * wab * (double)fb.z * v2;
         }
-        const int t = i - acc_lig;
-        const float4 ft = ff[t];
-        const int ht = __float_as_int(ft.w);
-        double gr = 0.0, gh = 0.0, gq = 0.0;
-        for (int r = 0; r < n_rows; ++r) {
-            const int ta = row_type[r];
-            const float4 fa = ff[ta];
-            const int ha = __float_as_int(fa.w);
-            for (int b = 0; b < n_types; ++b) {
-                const bool as_a = (ta == t), as_b = (b == t);
-                if (!as_a && !as_b) continue;
-                const double* v = sums + acc_lig + ((size_t)r * n_types + b) * 3;
-                const float4 fb = ff[b];
-                const int hb = __float_as_int(fb.w);
-                const double wab = ((ha == 1 && hb == 2) || (ha == 2 && hb == 1)) ? 2.0 : 1.0;
-                if (as_a) {
-                    gr += v[0];
-                    gh += 0.5 * v[1];
-                    gq += kKE * wab * (double)fb.z * v[2];
-                }
-                if (as_b) {
-                    gr += v[0];
-                    gh += 0.5 * v[1];
-                    gq += kKE * wab * (double)fa.z * v[2];
-                }
-            }
+        if (as_b) {
+            gr += v0;
+            gh += 0.5 * v1;
+            gq += kKE * wab * (double)fa.z * v2;
         }
-        (void)ht;
-        ff_grad[3 * t + 0] = (float)gr;
-        ff_grad[3 * t + 1] = (float)gh;
-        ff_grad[3 * t + 2] = (float)gq;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        gr += __shfl_xor_sync(0xffffffffu, gr, o);
+        gh += __shfl_xor_sync(0xffffffffu, gh, o);
+        gq += __shfl_xor_sync(0xffffffffu, gq, o);
+    }
+    __shared__ double s_w[3][8];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_w[0][w] = gr;
+        s_w[1][w] = gh;
+        s_w[2][w] = gq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            r0 += s_w[0][k];
+            r1 += s_w[1][k];
+            r2 += s_w[2][k];
+        }
+        ff_grad[3 * t + 0] = (float)r0;
+        ff_grad[3 * t + 1] = (float)r1;
+        ff_grad[3 * t + 2] = (float)r2;
     }
 }
 
@@ -409,9 +439,8 @@ cudaError_t launch_param_reduce(const double* cta_acc, int n_cta, int n_lig, int
     param_sum_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, s>>>(cta_acc, n_cta, acc_len, sums);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int outs = n_lig * 3 + n_types;
-    param_finish_kernel<<<(outs + 127) / 128, 128, 0, s>>>(sums, n_lig, n_rows, n_types,
-                                                            row_type, ff, lig_grad, ff_grad);
+    param_finish_kernel<<<n_types + 1, 256, 0, s>>>(sums, n_lig, n_rows, n_types, row_type, ff,
+                                                     lig_grad, ff_grad);
     return cudaGetLastError();
 }
 
