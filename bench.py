@@ -350,8 +350,20 @@ def refine_throughput(bude, synth, tune, dev, timed, variant="fast", steps=10):
     same = bool(torch.equal(Pa, P) and torch.equal(Ea, E))
     deck.close()
     t = statistics.mean(ms)
+    # the graph evaluates the adjoint steps + 1 times (the start and each
+    # trial); the two element-wise kernels per step are negligible beside it
+    m = MEASURED_EXECUTED_ADJOINT
+    executed = None
+    if (kernel_sha(), variant, o.ppwi) == (m["kernel_sha256_16"], m["variant"], m["ppwi"]):
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        tf = m["flop_per_pair"] * 64 * 2672 * P.shape[1] * (steps + 1) / (t / 1e3) / 1e12
+        executed = {"adjoint_evaluations": steps + 1, "flop_per_pair": m["flop_per_pair"],
+                    "tflops": tf, "frac_fp32_peak": tf / peak,
+                    "source": "the adjoint's ncu opcode counters; time of the whole graph"}
     return {"workload": f"{steps} steps x 16384 poses, 64 lig x 2672 pro, seed 4",
             "variant": variant, "ms": t, "pose_steps_per_s": steps * P.shape[1] / (t / 1e3),
+            "executed": executed,
             "graph_launches_per_call": 1, "kernels_per_call": launches // 5,
             "mean_energy_before": e0, "mean_energy_after": Ea.mean().item(),
             "cull_ms": statistics.mean(ms_c), "cull_bit_identical": same}
