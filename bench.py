@@ -272,9 +272,16 @@ def batched_vs_plain(bude, synth, tune, dev, timed, variant="fast", count=64, se
     for d in decks:
         d.close()
     tb, tp = statistics.mean(ms_b), statistics.mean(ms_p)
+    # Eq. 3 in the many-poses limit, summed over the decks, against the FP32 peak
+    alg = sum(algorithmic_flops(len(d["lig_type"]), len(d["pro_type"]), d["poses"].shape[1])
+              for d in decks_np)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     return {"workload": f"{count} decks, log-uniform lig 8-128, pro 500-5000, poses 1024-65536, seed {seed}",
             "variant": variant, "poses": n, "pair_evaluations": pairs,
             "batched_ms": tb, "plain_ms": tp, "speedup": tp / tb,
+            "batched_eq3_frac_fp32_peak": alg / (tb / 1e3) / 1e12 / peak,
+            "plain_eq3_frac_fp32_peak": alg / (tp / 1e3) / 1e12 / peak,
             "batched_poses_per_s": n / (tb / 1e3), "plain_poses_per_s": n / (tp / 1e3),
             "batched_launches": lb // 10, "plain_launches": plain_launches[0],
             "batched_opts": {"ppwi": ob.ppwi, "block": ob.block, "ctas_per_sm": ob.ctas_per_sm},
