@@ -83,3 +83,26 @@ def test_surviving_quartet_count_matches_a_host_count():
     with pytest.raises(bude.BudeError):
         hf.quartets(-1.0)
     hf.close()
+
+
+@pytest.mark.parametrize("variant", ["fp64", "ieee"])
+def test_everything_screened_gives_zero_and_screening_is_monotone(variant):
+    # a threshold above every Schwarz product leaves no quartet (every warp's
+    # range is empty) and G = 0
+    s = synth.make_he_lattice(13, 12, 3)
+    hf = bude.HartreeFock(s["geom"], s["xpnt"], s["coef"], device=DEV)
+    D = torch.from_numpy(s["dens"]).to(DEV)
+    assert hf.quartets(1e30) == 0
+    G = hf.fock(D, tol=1e30, variant=variant)
+    torch.cuda.synchronize()
+    assert torch.all(G == 0)
+    # the surviving set only grows as the threshold falls, to every unique
+    # quartet at 0; a coarse threshold removes some and changes G
+    counts = [hf.quartets(t) for t in (1e30, 1e-2, 1e-6, 1e-10, 0.0)]
+    m = 12 * 13 // 2
+    assert counts == sorted(counts) and counts[-1] == m * (m + 1) // 2
+    full = hf.fock(D, tol=0.0, variant=variant).cpu().numpy()
+    coarse = hf.fock(D, tol=1e-2, variant=variant).cpu().numpy()
+    assert counts[1] < counts[-1]
+    assert np.abs(coarse - full).max() > 1e-6 * np.abs(full).max()
+    hf.close()
