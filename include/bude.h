@@ -81,7 +81,12 @@ typedef struct {
 /*
  * Launch options.  Zero in any field selects the library default for the
  * variant (the defaults come from the autotuner's tables compiled in or set
- * with bude_set_default_options).
+ * with bude_set_default_options).  The defaults are one shape per variant,
+ * shared by all calls: a gradient call (bude_pose_grad, bude_refine) takes at
+ * most 8 poses per thread (FP64: 4) and, when its block comes from the
+ * defaults, at most as many threads as the adjoint kernel's registers let
+ * one CTA hold.  An explicit block that cannot be resident returns
+ * BUDE_ERR_UNSUPPORTED.
  */
 typedef struct {
     int32_t variant;     /* BUDE_FP32_IEEE .. BUDE_FP64 */

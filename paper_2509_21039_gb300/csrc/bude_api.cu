@@ -219,9 +219,23 @@ int resolve_options(const bude_options* o, bool G, Resolved* r)
         return fail(BUDE_ERR_INVALID_ARG, "block %d: need a multiple of 32 in [64, 1024]", r->block);
     if (r->tile < 0) return fail(BUDE_ERR_INVALID_ARG, "tile %d < 0", r->tile);
     if (r->cps < 1 || r->cps > 32) return fail(BUDE_ERR_INVALID_ARG, "ctas_per_sm %d", r->cps);
-    if (!kernel_for(variant, r->P, G))
+    const void* fn = kernel_for(variant, r->P, G);
+    if (!fn)
         return fail(BUDE_ERR_UNSUPPORTED, "poses per thread %d not built for variant %d%s", r->P,
                     variant, G ? " (adjoint)" : "");
+    // The defaults are one shape per variant, usually the energy kernel's; an
+    // adjoint call that takes its block from them gets at most as many
+    // threads as the adjoint kernel's registers let one CTA have (an explicit
+    // block is left as asked, and fails at launch if it cannot be resident).
+    if (G && !(o && o->block)) {
+        const void* fk = r->cull ? kernel_for(variant, r->P, G, true) : nullptr;
+        if (!fk) fk = fn;
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, fk) == cudaSuccess) {
+            const int cap = fa.maxThreadsPerBlock / 32 * 32;
+            if (cap >= 64 && r->block > cap) r->block = cap;
+        }
+    }
     return BUDE_OK;
 }
 

@@ -452,3 +452,30 @@ def test_autograd_function_and_refinement():
 def test_ieee_square_root_is_correctly_rounded_everywhere():
     mism, first = bude.selfcheck_sqrt()
     assert mism == 0, f"{mism} mismatches, first at bits {first:#010x}"
+
+
+@pytest.mark.parametrize("variant", ["ieee", "fast", "fp64"])
+def test_gradient_with_energy_shaped_defaults(variant):
+    # the defaults hold one shape per variant, here the energy kernel's widest
+    # (P = 16 or 4 with 384 threads, more threads than the adjoint kernel's
+    # registers allow): a gradient call without options still runs, with the
+    # block cut to what the adjoint kernel can hold, and matches an explicit shape
+    D = synth.make_deck(171, 12, 300, 34, 700)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    saved = bude.default_options(variant)
+    try:
+        wide = bude.LaunchOptions(variant=variant, ppwi=4 if variant == "fp64" else 16, block=384,
+                                  ctas_per_sm=1)
+        bude.set_default_options(wide)
+        e0, g0 = bude.pose_grad(deck, P, opts=bude.LaunchOptions(variant=variant))
+        e1, g1 = bude.pose_grad(deck, P, opts=bude.LaunchOptions(
+            variant=variant, ppwi=4 if variant == "fp64" else 8, block=128))
+        torch.cuda.synchronize()
+        tol = 1e-9 if variant == "fp64" else 1e-4
+        np.testing.assert_allclose(e0.cpu().numpy(), e1.cpu().numpy(), rtol=tol, atol=tol)
+        np.testing.assert_allclose(g0.cpu().numpy(), g1.cpu().numpy(), rtol=tol * 10, atol=tol * 10)
+        assert np.all(np.isfinite(e0.cpu().numpy()))
+    finally:
+        bude.set_default_options(saved)
+        deck.close()
