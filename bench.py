@@ -42,27 +42,27 @@ FP32_LANES_PER_SM = 128
 # profiles/pose_kernel_fast_64x2672x65536_launches.md).  Reported only
 # while the kernel source and the launch shape are the ones that were
 # measured.
-MEASURED_TRAFFIC = {"kernel_sha256_16": "19f29abd5002d932", "variant": "fast", "ppwi": 16,
-                    "block": 384, "bytes": 1849572.0}
+MEASURED_TRAFFIC = {"kernel_sha256_16": "41d527a5f5b7247c", "variant": "fast", "ppwi": 16,
+                    "block": 384, "bytes": 1863367.0}
 
 # FP32 FLOPs the kernel executes per pose-pair on the full deck, from ncu's
 # per-opcode thread-instruction counters of the same launch (FADD, FMUL 1;
 # FFMA, FADD2, FMUL2 2; FFMA2 4), per variant, for the kernel source with
 # this hash.  Fewer than Eq. 3's 30: zero desolvation runs are skipped, and
 # FAST rearranges the squared distance and the steric term.
-MEASURED_EXECUTED = {"kernel_sha256_16": "19f29abd5002d932",
+MEASURED_EXECUTED = {"kernel_sha256_16": "41d527a5f5b7247c",
                      "flop_per_pair": {"fast": 21.25, "ieee": 29.25, "comp": 29.24}}
 
 # The same count for the FAST adjoint (energies and pose gradients) at P = 8
 # on the 64 x 2672 x 16384 workload: the force and torque sums add the
 # reciprocal root's products and three FFMA2 per pose pair to the energy work.
-MEASURED_EXECUTED_ADJOINT = {"kernel_sha256_16": "19f29abd5002d932", "variant": "fast", "ppwi": 8,
+MEASURED_EXECUTED_ADJOINT = {"kernel_sha256_16": "41d527a5f5b7247c", "variant": "fast", "ppwi": 8,
                              "flop_per_pair": 36.77}
 
 # The same count for the FAST forcefield-gradient kernel (param_kernel) at
 # P = 8 on the 64 x 2672 x 16384 workload; the hash covers both of its
 # source files.
-MEASURED_EXECUTED_PARAM = {"kernel_sha256_16": "35ee3b55c9eaf157", "variant": "fast", "ppwi": 8,
+MEASURED_EXECUTED_PARAM = {"kernel_sha256_16": "66e50885d6bb26e2", "variant": "fast", "ppwi": 8,
                            "flop_per_pair": 39.12}
 
 

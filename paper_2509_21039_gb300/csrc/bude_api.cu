@@ -56,6 +56,9 @@ struct bude_deck {
     PairD* tabD = nullptr;
     int* row_type = nullptr; // [n_rows]
     float4* ff = nullptr;    // [n_types] forcefield rows as given
+    // ligand and protein atoms of a polar type (hbtype != 0): a pair has a
+    // desolvation term exactly when one of its atoms is polar
+    int lig_polar = 0, pro_polar = 0;
     // scratch workspace of the plain and adjoint calls
     double* partial = nullptr;
     size_t partial_bytes = 0;
@@ -270,6 +273,7 @@ int chunk_for(const InstanceShape& s, const Resolved& r, bool G, size_t budget)
 struct Plan {
     std::vector<Instance> inst;
     long long n_total = 0;
+    long long u_total = 0;  // cost of the flat space (the CTAs split it by cost)
     long long n_tiles = 0;
     size_t smem = 0;
     int grid = 0;
@@ -286,7 +290,7 @@ int make_plan(const std::vector<const bude_deck*>& decks, const std::vector<cons
     const size_t budget = smem_budget(di, r.cps);
     const long long TP = 32ll * r.P;
     pl->inst.clear();
-    long long k = 0, tiles = 0;
+    long long k = 0, tiles = 0, u = 0;
     size_t smem_max = 0;
     for (size_t i = 0; i < decks.size(); ++i) {
         const bude_deck* d = decks[i];
@@ -320,6 +324,16 @@ int make_plan(const std::vector<const bude_deck*>& decks, const std::vector<cons
         I.n_types = d->n_types;
         I.n_rows = d->n_rows;
         I.chunk = ch;
+        // cost of one pair iteration, in tenths of the kernels' cost units: 10
+        // for every pair plus 4 where the pair has a desolvation term (one of
+        // its atoms polar), averaged over the deck's pairs
+        {
+            const double lp = d->lig_polar, pp = d->pro_polar;
+            const double f = (lp * (d->n_pro - pp) + (d->n_lig - lp) * pp) / (double)K;
+            I.w = 10 * kCostPair + (int)std::llround(10.0 * kCostDesolv * f);
+        }
+        I.u_begin = u;
+        u += (I.k_end - I.k_begin) * (long long)I.w;
         k = I.k_end;
         tiles += nt;
         const size_t sm = smem_fixed(r.variant, r.P, G, r.block) +
@@ -330,6 +344,7 @@ int make_plan(const std::vector<const bude_deck*>& decks, const std::vector<cons
         pl->inst.push_back(I);
     }
     pl->n_total = k;
+    pl->u_total = u;
     pl->n_tiles = tiles;
     pl->smem = smem_max;
     pl->fn = kernel_for(r.variant, r.P, G, r.cull != 0);
@@ -443,6 +458,8 @@ int launch_plan(const Plan& pl, const Resolved& r, const Instance* dev_table, do
     if (a.n_inst == 1) a.single = pl.inst[0];
     a.table = dev_table;
     a.n_total = pl.n_total;
+    // one deck: the units all cost the same, split by count
+    a.u_total = a.n_inst > 1 ? pl.u_total : 0;
     a.partial = partial;
     a.counter = counter;
     a.err = device_err_word();
@@ -629,7 +646,7 @@ int bude_create_deck(const bude_deck_desc* desc, void* stream, bude_deck** out)
     d->n_lig = desc->n_lig;
     d->n_pro = desc->n_pro;
     d->n_types = desc->n_types;
-    struct Tmp { unsigned err; int n_rows; };
+    struct Tmp { unsigned err; int n_rows; int lig_polar; int pro_polar; };
     Tmp* tmp = nullptr;
     auto cleanup = [&](int code) {
         if (tmp) cudaFree(tmp);
@@ -662,8 +679,13 @@ int bude_create_deck(const bude_deck_desc* desc, void* stream, bude_deck** out)
                             d->n_types, d->lig, d->tabF, d->tabG, d->tabD, d->row_type,
                             &tmp->n_rows, &tmp->err, s),
         "pair table launch");
-    g_launches += (d->n_pro > 0) ? 2 : 1;
-    Tmp h{0, 0};
+    CKD(launch_count_polar((const float4*)desc->lig_xyzt, d->n_lig, d->ff, d->n_types,
+                           &tmp->lig_polar, s),
+        "polar count launch");
+    CKD(launch_count_polar(d->pro, d->n_pro, d->ff, d->n_types, &tmp->pro_polar, s),
+        "polar count launch");
+    g_launches += ((d->n_pro > 0) ? 2 : 1) + (d->n_lig > 0) + (d->n_pro > 0);
+    Tmp h{0, 0, 0, 0};
     CKD(cudaMemcpyAsync(&h, tmp, sizeof h, cudaMemcpyDeviceToHost, s), "readback");
     CKD(cudaStreamSynchronize(s), "deck synchronisation");
 #undef CKD
@@ -678,6 +700,8 @@ int bude_create_deck(const bude_deck_desc* desc, void* stream, bude_deck** out)
         return fail(BUDE_ERR_INVALID_ARG, "deck rejected:%s", why.c_str());
     }
     d->n_rows = h.n_rows;
+    d->lig_polar = h.lig_polar;
+    d->pro_polar = h.pro_polar;
     *out = d;
     return BUDE_OK;
 }

@@ -172,6 +172,34 @@ __global__ void sort_protein_kernel(const float4* __restrict__ src, float4* __re
     }
 }
 
+// Number of atoms whose type is polar (hbtype != 0).  A pair has a
+// desolvation term exactly when one of its two atoms is polar, so these two
+// counts give a deck's share of such pairs (its cost per pair iteration in a
+// batched launch).  Atoms with an invalid type are not counted (the deck is
+// rejected by the validation word anyway).
+__global__ void count_polar_kernel(const float4* __restrict__ atoms, int n,
+                                   const float4* __restrict__ ff, int n_types, int* __restrict__ count)
+{
+    int local = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int t = __float_as_int(atoms[i].w);
+        if (t >= 0 && t < n_types && __float_as_int(ff[t].w) != 0) ++local;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+}
+
+cudaError_t launch_count_polar(const float4* atoms, int n, const float4* ff, int n_types,
+                               int* count, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    int blocks = (n + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    count_polar_kernel<<<blocks, 256, 0, s>>>(atoms, n, ff, n_types, count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack_protein(const float4* src, float4* dst, int n, int n_types,
                                 unsigned* err, cudaStream_t s)
 {

@@ -39,6 +39,8 @@ const void* kernel_comp_cull(int P, bool G);
 
 cudaError_t launch_pack_protein(const float4* src, float4* dst, int n, int n_types,
                                 unsigned* err, cudaStream_t s);
+cudaError_t launch_count_polar(const float4* atoms, int n, const float4* ff, int n_types,
+                               int* count, cudaStream_t s);
 cudaError_t launch_build_tables(const float4* lig_src, int n_lig, const float4* ff, int n_types,
                                 float4* lig_dst, PairF* tabF, PairG* tabG, PairD* tabD,
                                 int* row_type, int* n_rows, unsigned* err, cudaStream_t s);

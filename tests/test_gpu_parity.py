@@ -352,6 +352,47 @@ def test_batched_uneven_against_oracle_and_plain():
         assert scaled_error(E, plain.astype(np.float64), np.abs(plain)).max() <= 2 * GATE["ieee"]
 
 
+@pytest.mark.parametrize("opts", [dict(variant="ieee"),
+                                  dict(variant="fast", ppwi=8, block=256, ctas_per_sm=4),
+                                  dict(variant="comp", ppwi=2, block=128, ctas_per_sm=2),
+                                  dict(variant="fp64", ppwi=1, block=128)])
+def test_batched_cost_weighted_split(opts):
+    # decks whose pairs cost differently (none, about half or most of them
+    # with a desolvation term) weight the CTAs' split of the flat space; with
+    # many CTAs and tiny decks some CTAs get no units at all
+    specs = [(0, 9, 300, 700), (1, 4, 50, 3), (2, 13, 800, 2100), (0, 2, 7, 40), (3, 20, 1500, 5000)]
+    decks_np = []
+    for i, (pattern, nl, npro, n) in enumerate(specs):
+        d = synth.make_deck([17, i], nl, npro, 12, n)
+        if pattern == 0:
+            d["hbtype"][:] = 0          # no polar type: no desolvation pair
+        elif pattern == 1:
+            d["hbtype"][:] = 1          # all polar: no desolvation pair either
+        elif pattern == 2:
+            d["hbtype"][:] = np.arange(12) % 2   # half polar
+        decks_np.append(d)
+    decks = [bude.Deck(d, device=DEV) for d in decks_np]
+    poses = [torch.from_numpy(d["poses"]).to(DEV) for d in decks_np]
+    o = bude.LaunchOptions(**opts)
+    outs = bude.energies_batched(decks, poses, opts=o)
+    outs2 = bude.energies_batched(decks, poses, opts=o)
+    torch.cuda.synchronize()
+    gate = GATE["fp64"] if opts["variant"] == "fp64" else GATE[opts["variant"]]
+    for d, p, out, out2, dnp in zip(decks, poses, outs, outs2, decks_np):
+        assert torch.equal(out, out2)
+        n = dnp["poses"].shape[1]
+        idx = np.unique(np.linspace(0, n - 1, min(n, 30)).astype(int))
+        ref, A = oracle.energies(dnp, dnp["poses"][:, idx], n_threads=-1, with_abs=True)
+        E = out.cpu().numpy()
+        assert scaled_error(E[idx], ref, A, opts["variant"]).max() <= gate
+        plain = bude.energies(d, p, opts=o).cpu().numpy()
+        # FP64: both are FP64 sums rounded once to float32, so within two ulps
+        between = 2.0 ** -22 if opts["variant"] == "fp64" else 2 * gate
+        assert scaled_error(E, plain.astype(np.float64), np.abs(plain)).max() <= between
+    for d in decks:
+        d.close()
+
+
 def test_batched_with_empty_instances():
     d0 = synth.make_deck(113, 6, 90, 8, 50)
     d1 = synth.make_deck(114, 6, 90, 8, 0)
