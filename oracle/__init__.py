@@ -66,6 +66,8 @@ def _load():
         lib.oracle_pose_grad.argtypes = deck_args + [i64, dp, dp, dp, dp, ci]
         lib.oracle_param_grad.restype = ci
         lib.oracle_param_grad.argtypes = deck_args + [i64, dp, dp, dp, dp]
+        lib.oracle_param_grad_scale.restype = ci
+        lib.oracle_param_grad_scale.argtypes = deck_args + [i64, dp, dp, dp, dp]
         lib.oracle_boys0.restype = cd
         lib.oracle_boys0.argtypes = [cd]
         lib.oracle_prim_eri.restype = cd
@@ -74,6 +76,8 @@ def _load():
         lib.oracle_eri.argtypes = [ci, dp, dp, dp, dp, dp, dp]
         lib.oracle_hf_fock_entries.restype = None
         lib.oracle_hf_fock_entries.argtypes = [ci, dp, ci, dp, dp, dp, ci, ip, ip, dp]
+        lib.oracle_hf_fock_scale_entries.restype = None
+        lib.oracle_hf_fock_scale_entries.argtypes = [ci, dp, ci, dp, dp, dp, ci, ip, ip, dp]
         lib.oracle_max_threads.restype = ci
         lib.oracle_max_threads.argtypes = []
         _lib = lib
@@ -174,22 +178,28 @@ def pose_grad(deck, poses, n_threads: int = 0, with_scale: bool = False):
     return (E, G, S) if with_scale else (E, G)
 
 
-def param_grad(deck, poses, weights=None):
+def param_grad(deck, poses, weights=None, with_scale: bool = False):
     """Gradient of L = sum_k w_k E_k (float64): (dL/d ligand xyz [n_lig][3],
-    dL/d (radius, hardness, elsc) [n_types][3])."""
+    dL/d (radius, hardness, elsc) [n_types][3]).  With with_scale, also the
+    per-element sums of the absolute values of the terms of each output
+    (oracle_param_grad_scale), same shapes: (GL, GF, SL, SF)."""
     lib = _load()
     args, keep = _deck_args(deck)
     P = np.ascontiguousarray(poses, np.float64).reshape(6, -1)
     n = P.shape[1]
     w = None if weights is None else np.ascontiguousarray(weights, np.float64)
+    wp = _dptr(w) if w is not None else None
     GL = np.zeros((len(deck["lig_type"]), 3), np.float64)
     GF = np.zeros((len(deck["radius"]), 3), np.float64)
-    rc = lib.oracle_param_grad(*args, n, _dptr(P), _dptr(w) if w is not None else None,
-                               _dptr(GL), _dptr(GF))
+    rc = lib.oracle_param_grad(*args, n, _dptr(P), wp, _dptr(GL), _dptr(GF))
+    if rc == 0 and with_scale:
+        SL = np.zeros_like(GL)
+        SF = np.zeros_like(GF)
+        rc = lib.oracle_param_grad_scale(*args, n, _dptr(P), wp, _dptr(SL), _dptr(SF))
     del keep
     if rc != 0:
         raise ValueError("oracle_param_grad rejected the deck")
-    return GL, GF
+    return (GL, GF, SL, SF) if with_scale else (GL, GF)
 
 
 # --- pose refinement (the docking step after scoring) ----------------------
@@ -260,6 +270,29 @@ def hf_fock_entries(geom, xpnt, coef, dens, rows, cols):
     _load().oracle_hf_fock_entries(n, _dptr(g), len(x), _dptr(x), _dptr(c), _dptr(d), len(r),
                                    _iptr(r), _iptr(k), _dptr(out))
     return out
+
+
+def hf_fock_scale_entries(geom, xpnt, coef, dens, rows, cols):
+    """S_ij = sum_kl |D_kl| (2 |(ij|kl)| + |(ik|jl)|) for the listed (i, j):
+    the sum of G_ij's terms in absolute value."""
+    g = np.ascontiguousarray(geom, np.float64).reshape(-1, 3)
+    n = g.shape[0]
+    x = np.ascontiguousarray(xpnt, np.float64)
+    c = np.ascontiguousarray(coef, np.float64)
+    d = np.ascontiguousarray(dens, np.float64).reshape(n, n)
+    r = np.ascontiguousarray(rows, np.int32)
+    k = np.ascontiguousarray(cols, np.int32)
+    out = np.zeros(len(r), np.float64)
+    _load().oracle_hf_fock_scale_entries(n, _dptr(g), len(x), _dptr(x), _dptr(c), _dptr(d),
+                                         len(r), _iptr(r), _iptr(k), _dptr(out))
+    return out
+
+
+def hf_fock_scale(geom, xpnt, coef, dens):
+    """The full S matrix of hf_fock_scale_entries (small systems)."""
+    n = np.asarray(geom).reshape(-1, 3).shape[0]
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    return hf_fock_scale_entries(geom, xpnt, coef, dens, ii.ravel(), jj.ravel()).reshape(n, n)
 
 
 def hf_fock(geom, xpnt, coef, dens):

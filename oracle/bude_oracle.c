@@ -456,3 +456,80 @@ int oracle_param_grad(int n_lig, const double* lig_xyz, const int32_t* lig_type,
     }
     return 0;
 }
+
+/*
+ * Parity scales of oracle_param_grad: every output element is a sum of
+ * terms, one per (pose, ligand atom, protein atom[, component]); each scale
+ * element is the same sum with every term replaced by its absolute value,
+ * and the three parts of de/dR and of de/dd (steric, electrostatic,
+ * desolvation) taken as separate terms.  The rounding error of a computed
+ * sum is bounded by a small multiple of the unit roundoff times this sum of
+ * absolute values (the standard bound for recursive summation), so it is
+ * the scale against which a lower-precision result of the same sum is
+ * judged element by element.  Same arguments as oracle_param_grad;
+ * lig_scale is [n_lig][3], ff_scale [n_types][3].
+ */
+int oracle_param_grad_scale(int n_lig, const double* lig_xyz, const int32_t* lig_type,
+                            int n_pro, const double* pro_xyz, const int32_t* pro_type,
+                            int n_types, const double* radius, const double* hardness,
+                            const double* elsc, const int32_t* hbtype,
+                            int64_t n_poses, const double* poses, const double* weights,
+                            double* lig_scale, double* ff_scale)
+{
+    oracle_deck D = {n_lig, n_pro, n_types, lig_xyz, lig_type, pro_xyz,
+                     pro_type, radius, hardness, elsc, hbtype};
+    if (n_poses < 0 || check_deck(&D) != 0) return -1;
+    for (int i = 0; i < 3 * n_lig; ++i) lig_scale[i] = 0.0;
+    for (int i = 0; i < 3 * n_types; ++i) ff_scale[i] = 0.0;
+    for (int64_t k = 0; k < n_poses; ++k) {
+        double wk = fabs(weights ? weights[k] : 1.0);
+        double R[9];
+        oracle_rotation(poses[0 * n_poses + k], poses[1 * n_poses + k],
+                        poses[2 * n_poses + k], R);
+        double t[3] = {poses[3 * n_poses + k], poses[4 * n_poses + k],
+                       poses[5 * n_poses + k]};
+        for (int l = 0; l < n_lig; ++l) {
+            const double* x = lig_xyz + 3 * l;
+            double xp[3];
+            for (int i = 0; i < 3; ++i)
+                xp[i] = R[3 * i + 0] * x[0] + R[3 * i + 1] * x[1] +
+                        R[3 * i + 2] * x[2] + t[i];
+            int a = lig_type[l];
+            for (int p = 0; p < n_pro; ++p) {
+                int b = pro_type[p];
+                const double* y = pro_xyz + 3 * p;
+                double dv[3] = {xp[0] - y[0], xp[1] - y[1], xp[2] - y[2]};
+                double d = sqrt(dot3(dv, dv));
+                pair_params pp = deck_pair(&D, a, b);
+                double s = d - pp.R;
+                /* the parts of de/dd, each as an absolute value */
+                double e_el = fabs(pp.QW * switch_dphi(s / ORACLE_DE) / ORACLE_DE);
+                double e_de = fabs(pp.S * switch_dphi(s / ORACLE_DD) / ORACLE_DD);
+                double e_st = 0.0, r_st = 0.0, dH = 0.0;
+                if (s < 0.0) {
+                    e_st = fabs(2.0 * pp.H * s / (pp.R * pp.R));
+                    r_st = fabs(2.0 * pp.H * (s / pp.R) * d / (pp.R * pp.R));
+                    dH = (s / pp.R) * (s / pp.R);
+                }
+                double wab = ((hbtype[a] == 1 && hbtype[b] == 2) ||
+                              (hbtype[a] == 2 && hbtype[b] == 1)) ? 2.0 : 1.0;
+                double phiE = switch_phi(s / ORACLE_DE);
+                double f = 0.5 * wk;
+                double r_abs = r_st + e_el + e_de;
+                ff_scale[3 * a + 0] += f * r_abs;
+                ff_scale[3 * b + 0] += f * r_abs;
+                ff_scale[3 * a + 1] += f * 0.5 * dH;
+                ff_scale[3 * b + 1] += f * 0.5 * dH;
+                ff_scale[3 * a + 2] += f * ORACLE_KE * wab * fabs(elsc[b]) * phiE;
+                ff_scale[3 * b + 2] += f * ORACLE_KE * wab * fabs(elsc[a]) * phiE;
+                if (d > 0.0) {
+                    double c = (e_st + e_el + e_de) / d;
+                    for (int j = 0; j < 3; ++j)
+                        for (int i = 0; i < 3; ++i)
+                            lig_scale[3 * l + j] += f * fabs(R[3 * i + j]) * c * fabs(dv[i]);
+                }
+            }
+        }
+    }
+    return 0;
+}

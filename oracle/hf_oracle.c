@@ -86,3 +86,28 @@ void oracle_hf_fock_entries(int n, const double* geom, int ng, const double* xpn
         out[e] = g;
     }
 }
+
+/*
+ * Parity scale of G_ij: the plain sum above with every term replaced by its
+ * absolute value, S_ij = sum_kl |D_kl| (2 |(ij|kl)| + |(ik|jl)|).  The
+ * rounding error of any evaluation of G_ij as a sum of these terms is
+ * bounded by a small multiple of the unit roundoff times S_ij.
+ */
+void oracle_hf_fock_scale_entries(int n, const double* geom, int ng, const double* xpnt,
+                                  const double* coef, const double* dens, int n_entries,
+                                  const int32_t* rows, const int32_t* cols, double* out)
+{
+    for (int e = 0; e < n_entries; ++e) {
+        int i = rows[e], j = cols[e];
+        double g = 0.0;
+        for (int k = 0; k < n; ++k)
+            for (int l = 0; l < n; ++l) {
+                double J = oracle_eri(ng, xpnt, coef, geom + 3 * i, geom + 3 * j,
+                                      geom + 3 * k, geom + 3 * l);
+                double K = oracle_eri(ng, xpnt, coef, geom + 3 * i, geom + 3 * k,
+                                      geom + 3 * j, geom + 3 * l);
+                g += fabs(dens[k * n + l]) * (2.0 * fabs(J) + fabs(K));
+            }
+        out[e] = g;
+    }
+}

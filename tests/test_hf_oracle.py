@@ -72,3 +72,45 @@ def test_fock_structure():
     D1 = np.array([[0.7]])
     e = oracle.eri(s["xpnt"], s["coef"], g1[0], g1[0], g1[0], g1[0])
     assert oracle.hf_fock(g1, s["xpnt"], s["coef"], D1)[0, 0] == pytest.approx(0.7 * e, rel=1e-13)
+
+
+# --- parity scale of the Fock term ----------------------------------------
+#
+# S_ij = sum_kl |D_kl| (2 |(ij|kl)| + |(ik|jl)|) bounds |G_ij| and every
+# rounding of it; pinned by closed forms on one atom and on atoms far apart.
+
+def test_fock_scale_bounds_g():
+    s = synth.make_he_lattice(4, 6, 3)
+    D = s["dens"] * np.random.default_rng(1).choice([-1.0, 1.0], size=s["dens"].shape)
+    D = 0.5 * (D + D.T)
+    G = oracle.hf_fock(s["geom"], s["xpnt"], s["coef"], D)
+    S = oracle.hf_fock_scale(s["geom"], s["xpnt"], s["coef"], D)
+    assert np.all(np.abs(G) <= S * (1 + 1e-13))
+    assert np.any(S > 1.5 * np.abs(G))
+
+
+def test_fock_scale_one_atom_is_three_times_g():
+    # one primitive on one atom: G = D (00|00) and S = 3 |D| (00|00), with
+    # (00|00) = 2 sqrt(x / pi) for a normalised primitive of exponent x
+    x = 0.9
+    g1 = np.zeros((1, 3))
+    for d in (0.7, -0.4):
+        D1 = np.array([[d]])
+        G = oracle.hf_fock(g1, [x], [1.0], D1)[0, 0]
+        S = oracle.hf_fock_scale(g1, [x], [1.0], D1)[0, 0]
+        assert G == pytest.approx(d * 2 * math.sqrt(x / math.pi), rel=1e-13)
+        assert S == pytest.approx(3 * abs(d) * 2 * math.sqrt(x / math.pi), rel=1e-13)
+
+
+def test_fock_scale_far_apart_exchange_term():
+    """Diagonal non-negative density on atoms 60 bohr apart: the exchange
+    integrals (ik|ik) vanish for i != k, so S_ii - G_ii = 2 sum_k D_kk (ik|ik)
+    = 2 D_ii (ii|ii), the one-centre closed form."""
+    x = 1.3
+    g = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 60.0], [0.0, 60.0, 0.0]])
+    D = np.diag([0.3, 0.8, 0.5])
+    G = oracle.hf_fock(g, [x], [1.0], D)
+    S = oracle.hf_fock_scale(g, [x], [1.0], D)
+    one = 2 * math.sqrt(x / math.pi)
+    for i in range(3):
+        assert S[i, i] - G[i, i] == pytest.approx(2 * D[i, i] * one, rel=1e-12)

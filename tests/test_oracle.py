@@ -420,3 +420,81 @@ def test_param_grad_scaling_identities():
     L_elec = oracle.energies(dict(D, hardness=np.zeros_like(D["hardness"])), P).sum()
     assert np.dot(D["hardness"], GF[:, 1]) == pytest.approx(L_ster, rel=1e-10, abs=1e-10)
     assert np.dot(D["elsc"], GF[:, 2]) == pytest.approx(2 * L_elec, rel=1e-10, abs=1e-10)
+
+
+# --- parity scales of the forcefield gradient ------------------------------
+#
+# oracle.param_grad(..., with_scale=True) also returns, per output element,
+# the sum of its terms in absolute value (the bound on the rounding of any
+# evaluation of that sum).  Pins: it bounds the gradient, it equals the
+# gradient's magnitude where a single term makes up the element, it splits
+# de/dd into its steric, electrostatic and desolvation parts, and it grows
+# with |w|, not w.
+
+def test_param_grad_scale_bounds_the_gradient():
+    D = _as64(synth.make_deck(33, 7, 180, 6, 14))
+    w = np.random.default_rng(5).uniform(-1.5, 1.5, 14)
+    GL, GF, SL, SF = oracle.param_grad(D, D["poses"], w, with_scale=True)
+    assert np.all(np.abs(GL) <= SL * (1 + 1e-12) + 1e-300)
+    assert np.all(np.abs(GF) <= SF * (1 + 1e-12) + 1e-300)
+    # with weights of both signs some elements cancel, so the bound is strict there
+    assert np.any(SF > 1.01 * np.abs(GF))
+    # the scale of w equals the scale of |w| and is linear in it
+    _, _, SL2, SF2 = oracle.param_grad(D, D["poses"], np.abs(w), with_scale=True)
+    np.testing.assert_allclose(SL2, SL, rtol=1e-14)
+    np.testing.assert_allclose(SF2, SF, rtol=1e-14)
+    _, _, SL3, SF3 = oracle.param_grad(D, D["poses"], 2.0 * w, with_scale=True)
+    np.testing.assert_allclose(SL3, 2.0 * SL, rtol=1e-14)
+    np.testing.assert_allclose(SF3, 2.0 * SF, rtol=1e-14)
+
+
+def _pair_scale(ta, tb, d, w=None):
+    D = _single_pair_deck(ta, tb, d)
+    P = np.zeros((6, 1 if w is None else len(w)))
+    return oracle.param_grad(D, P, w, with_scale=True)
+
+
+@pytest.mark.parametrize("ta,tb,d", [
+    ((1.5, 10.0, 0.0, 0), (1.5, 30.0, 0.0, 0), 2.0),    # steric only
+    ((1.5, 0.0, 0.5, 1), (1.5, 0.0, -0.5, 2), 4.0),     # electrostatics only
+    ((1.5, 0.0, 0.0, 1), (2.0, 0.0, 0.0, 0), 4.5),      # desolvation only
+])
+def test_param_grad_scale_equals_a_single_term(ta, tb, d):
+    GL, GF, SL, SF = _pair_scale(ta, tb, d)
+    np.testing.assert_allclose(SL, np.abs(GL), rtol=1e-14, atol=1e-300)
+    np.testing.assert_allclose(SF, np.abs(GF), rtol=1e-14, atol=1e-300)
+    assert SL[0, 0] > 0 and SL[0, 1] == 0 and SL[0, 2] == 0
+
+
+def test_param_grad_scale_keeps_the_terms_apart():
+    """Electrostatics (opposite charges) and desolvation both act at d = 4 and
+    their derivatives have opposite signs: the scale is the sum of the two
+    single-term magnitudes, the gradient only their difference."""
+    both = ((1.5, 0.0, 0.5, 1), (1.5, 0.0, -0.5, 0))
+    elec = ((1.5, 0.0, 0.5, 1), (1.5, 0.0, -0.5, 1))     # same Q w, no desolvation
+    desolv = ((1.5, 0.0, 0.0, 1), (1.5, 0.0, 0.0, 0))    # same S, no charges
+    d = 4.0
+    de_el = oracle.pair_denergy(*elec, d)
+    de_de = oracle.pair_denergy(*desolv, d)
+    assert de_el > 0 > de_de
+    GL, GF, SL, SF = _pair_scale(*both, d)
+    assert SL[0, 0] == pytest.approx(0.5 * (abs(de_el) + abs(de_de)), rel=1e-14)
+    assert abs(GL[0, 0]) == pytest.approx(0.5 * abs(de_el + de_de), rel=1e-14)
+    for t in (0, 1):   # de/dR = -de/dd here (s > 0): the same two parts
+        assert SF[t, 0] == pytest.approx(0.5 * (abs(de_el) + abs(de_de)), rel=1e-14)
+    # de/dq_a = K_E w q_b phi(s/D_E): 4 * 1 * (-0.5) * phi(1/4) / 2, phi(1/4) = 0.84375
+    assert GF[0, 2] == pytest.approx(-0.84375, rel=1e-14)
+    assert SF[0, 2] == pytest.approx(0.84375, rel=1e-14)
+    assert SF[1, 2] == pytest.approx(0.84375, rel=1e-14)
+    assert SF[0, 1] == 0 and SF[1, 1] == 0       # no overlap: no hardness term
+
+
+def test_param_grad_scale_counts_cancelling_poses():
+    """The same pose twice with weights +1 and -1: the gradient cancels to 0,
+    the scale is twice that of one pose."""
+    ta, tb, d = (1.5, 10.0, 0.0, 0), (1.5, 30.0, 0.0, 0), 2.0
+    GL1, GF1, SL1, SF1 = _pair_scale(ta, tb, d)
+    GL, GF, SL, SF = _pair_scale(ta, tb, d, np.array([1.0, -1.0]))
+    assert np.all(GL == 0) and np.all(GF == 0)
+    np.testing.assert_allclose(SL, 2 * SL1, rtol=1e-14)
+    np.testing.assert_allclose(SF, 2 * SF1, rtol=1e-14)
