@@ -49,7 +49,9 @@ Range::~Range() { nvtxRangePop(); }
 struct bude_deck {
     int device = 0;
     int n_lig = 0, n_pro = 0, n_types = 0, n_rows = 0;
-    float4* pro = nullptr;   // [n_pro]
+    float4* pro = nullptr;   // [n_pro] sorted by type, coordinates as given (FP64 kernel)
+    float4* pro_c = nullptr; // [n_pro] the same atoms in the frame centred on centre[] (FP32 kernels)
+    float centre[3] = {0.f, 0.f, 0.f};  // midpoint of the protein's bounding box
     float4* lig = nullptr;   // [n_lig] row-mapped
     PairF* tabF = nullptr;   // [n_rows][n_types]
     PairG* tabG = nullptr;
@@ -195,6 +197,7 @@ size_t smem_fixed(int variant, int P, bool G, int block)
 
 // Static shared memory of the kernel (Instance + flag), rounded up.
 constexpr size_t kStaticSmem = 256;
+static_assert(sizeof(Instance) + sizeof(int) <= kStaticSmem, "static shared memory of pose_kernel");
 
 struct Resolved {
     int variant, P, block, tile, cps, cull;
@@ -304,7 +307,13 @@ int make_plan(const std::vector<const bude_deck*>& decks, const std::vector<cons
                         d->n_types);
         Instance I;
         memset(&I, 0, sizeof I);
-        I.pro = d->pro;
+        // FP32 kernels: the recentred copy, with the origin subtracted from
+        // the translations; FP64: the atoms as given (exact in double)
+        const bool f64 = r.variant == BUDE_FP64;
+        I.pro = f64 ? d->pro : d->pro_c;
+        I.ox = f64 ? 0.f : d->centre[0];
+        I.oy = f64 ? 0.f : d->centre[1];
+        I.oz = f64 ? 0.f : d->centre[2];
         I.lig = d->lig;
         // packed kernels stage their records from the adjoint table, which
         // also holds the steric factors sqrt|H|/R and sqrt|H|
@@ -646,7 +655,7 @@ int bude_create_deck(const bude_deck_desc* desc, void* stream, bude_deck** out)
     d->n_lig = desc->n_lig;
     d->n_pro = desc->n_pro;
     d->n_types = desc->n_types;
-    struct Tmp { unsigned err; int n_rows; int lig_polar; int pro_polar; };
+    struct Tmp { unsigned err; int n_rows; int lig_polar; int pro_polar; float centre[4]; };
     Tmp* tmp = nullptr;
     auto cleanup = [&](int code) {
         if (tmp) cudaFree(tmp);
@@ -662,6 +671,7 @@ int bude_create_deck(const bude_deck_desc* desc, void* stream, bude_deck** out)
     const size_t pairs = (size_t)std::max(1, d->n_lig < d->n_types ? d->n_lig : d->n_types) *
                          d->n_types;
     CKD(dev_alloc((void**)&d->pro, np * sizeof(float4)), "deck allocation");
+    CKD(dev_alloc((void**)&d->pro_c, np * sizeof(float4)), "deck allocation");
     CKD(dev_alloc((void**)&d->lig, nl * sizeof(float4)), "deck allocation");
     CKD(dev_alloc((void**)&d->tabF, pairs * sizeof(PairF)), "deck allocation");
     CKD(dev_alloc((void**)&d->tabG, pairs * sizeof(PairG)), "deck allocation");
@@ -684,8 +694,10 @@ int bude_create_deck(const bude_deck_desc* desc, void* stream, bude_deck** out)
         "polar count launch");
     CKD(launch_count_polar(d->pro, d->n_pro, d->ff, d->n_types, &tmp->pro_polar, s),
         "polar count launch");
-    g_launches += ((d->n_pro > 0) ? 2 : 1) + (d->n_lig > 0) + (d->n_pro > 0);
-    Tmp h{0, 0, 0, 0};
+    CKD(launch_recentre_protein(d->pro, d->pro_c, d->n_pro, tmp->centre, s),
+        "protein recentring launch");
+    g_launches += ((d->n_pro > 0) ? 3 : 1) + (d->n_lig > 0) + (d->n_pro > 0);
+    Tmp h{0, 0, 0, 0, {0.f, 0.f, 0.f, 0.f}};
     CKD(cudaMemcpyAsync(&h, tmp, sizeof h, cudaMemcpyDeviceToHost, s), "readback");
     CKD(cudaStreamSynchronize(s), "deck synchronisation");
 #undef CKD
@@ -702,6 +714,7 @@ int bude_create_deck(const bude_deck_desc* desc, void* stream, bude_deck** out)
     d->n_rows = h.n_rows;
     d->lig_polar = h.lig_polar;
     d->pro_polar = h.pro_polar;
+    for (int j = 0; j < 3; ++j) d->centre[j] = h.centre[j];
     *out = d;
     return BUDE_OK;
 }
@@ -714,6 +727,7 @@ int bude_destroy_deck(bude_deck* d)
     drop_refines_using(d);
     cudaDeviceSynchronize();
     cudaFree(d->pro);
+    cudaFree(d->pro_c);
     cudaFree(d->lig);
     cudaFree(d->tabF);
     cudaFree(d->tabG);
@@ -1203,7 +1217,10 @@ extern "C" BUDE_API int bude_param_grad(bude_deck* deck, const float* poses, int
     if (rc) return rc;
     ParamArgs a;
     memset(&a, 0, sizeof a);
-    a.pro = deck->pro;
+    a.pro = deck->pro_c;
+    a.ox = deck->centre[0];
+    a.oy = deck->centre[1];
+    a.oz = deck->centre[2];
     a.lig = deck->lig;
     a.pair = deck->tabG;
     a.poses = poses;

@@ -172,6 +172,55 @@ __global__ void sort_protein_kernel(const float4* __restrict__ src, float4* __re
     }
 }
 
+// Single CTA: the midpoint c of the protein's bounding box, and the copy
+// p - c of every atom, rounded once to FP32, with its type kept.  The FP32
+// kernels work in this frame (they subtract c from the pose translations):
+// the energy only depends on differences x' - p, and small coordinates keep
+// the rounding of x' and of the squared distance small wherever the deck
+// sits.  min and max are exact and order-free, so c is the same on every
+// run.  n >= 1.
+__global__ void recentre_protein_kernel(const float4* __restrict__ src, float4* __restrict__ dst,
+                                        int n, float* __restrict__ centre)
+{
+    __shared__ float s_lo[3][32], s_hi[3][32];
+    __shared__ float s_c[3];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+    for (int i = tid; i < n; i += blockDim.x) {
+        const float4 a = src[i];
+        lo[0] = fminf(lo[0], a.x); hi[0] = fmaxf(hi[0], a.x);
+        lo[1] = fminf(lo[1], a.y); hi[1] = fmaxf(hi[1], a.y);
+        lo[2] = fminf(lo[2], a.z); hi[2] = fmaxf(hi[2], a.z);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[j] = fminf(lo[j], __shfl_xor_sync(0xffffffffu, lo[j], o));
+            hi[j] = fmaxf(hi[j], __shfl_xor_sync(0xffffffffu, hi[j], o));
+        }
+        if (lane == 0) { s_lo[j][warp] = lo[j]; s_hi[j][warp] = hi[j]; }
+    }
+    __syncthreads();
+    if (tid < 3) {
+        float l = s_lo[tid][0], h = s_hi[tid][0];
+        for (int w = 1; w < nwarps; ++w) { l = fminf(l, s_lo[tid][w]); h = fmaxf(h, s_hi[tid][w]); }
+        float c = 0.5f * l + 0.5f * h;
+        // a deck with a non-finite coordinate is rejected by the validation
+        // pass; keep its frame finite meanwhile
+        if (!isfinite(c)) c = 0.f;
+        s_c[tid] = c;
+        centre[tid] = c;
+    }
+    __syncthreads();
+    const float cx = s_c[0], cy = s_c[1], cz = s_c[2];
+    for (int i = tid; i < n; i += blockDim.x) {
+        const float4 a = src[i];
+        dst[i] = make_float4(a.x - cx, a.y - cy, a.z - cz, a.w);
+    }
+}
+
 // Number of atoms whose type is polar (hbtype != 0).  A pair has a
 // desolvation term exactly when one of its two atoms is polar, so these two
 // counts give a deck's share of such pairs (its cost per pair iteration in a
@@ -197,6 +246,14 @@ cudaError_t launch_count_polar(const float4* atoms, int n, const float4* ff, int
     int blocks = (n + 255) / 256;
     if (blocks > 1024) blocks = 1024;
     count_polar_kernel<<<blocks, 256, 0, s>>>(atoms, n, ff, n_types, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recentre_protein(const float4* src, float4* dst, int n, float* centre,
+                                    cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    recentre_protein_kernel<<<1, 1024, 0, s>>>(src, dst, n, centre);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,10 @@ const void* kernel_comp_cull(int P, bool G);
 
 cudaError_t launch_pack_protein(const float4* src, float4* dst, int n, int n_types,
                                 unsigned* err, cudaStream_t s);
+// The midpoint of the protein's bounding box (centre[0..2]) and the copy
+// dst = src - centre of every atom (types kept).
+cudaError_t launch_recentre_protein(const float4* src, float4* dst, int n, float* centre,
+                                    cudaStream_t s);
 cudaError_t launch_count_polar(const float4* atoms, int n, const float4* ff, int n_types,
                                int* count, cudaStream_t s);
 cudaError_t launch_build_tables(const float4* lig_src, int n_lig, const float4* ff, int n_types,
@@ -47,7 +51,7 @@ cudaError_t launch_build_tables(const float4* lig_src, int n_lig, const float4* 
 
 // Forcefield/ligand gradient kernel (bude_param.cu).
 struct ParamArgs {
-    const float4* pro;     // sorted by type
+    const float4* pro;     // sorted by type, in the frame with origin (ox, oy, oz)
     const float4* lig;     // row-mapped
     const PairG* pair;     // [n_rows][n_types]
     const float* poses;    // [6][n_poses]
@@ -56,6 +60,7 @@ struct ParamArgs {
     long long n_total;     // tiles * n_lig * n_pro
     double* cta_acc;       // [grid][n_lig*3 + n_rows*n_types*3]
     int n_lig, n_pro, n_types, n_rows, chunk;
+    float ox, oy, oz;      // subtracted from the pose translations (Instance::ox)
 };
 const void* kernel_param(int variant, int P);
 // Shared-memory bytes per staged protein atom of param_kernel: the packed

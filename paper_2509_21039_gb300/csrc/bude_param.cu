@@ -90,9 +90,9 @@ __global__ void param_kernel(const ParamArgs a)
             s_tr[6 * TP + s] = -sy;
             s_tr[7 * TP + s] = sx * cy;
             s_tr[8 * TP + s] = cx * cy;
-            s_tr[9 * TP + s] = a.poses[3 * n + k];
-            s_tr[10 * TP + s] = a.poses[4 * n + k];
-            s_tr[11 * TP + s] = a.poses[5 * n + k];
+            s_tr[9 * TP + s] = a.poses[3 * n + k] - a.ox;
+            s_tr[10 * TP + s] = a.poses[4 * n + k] - a.oy;
+            s_tr[11 * TP + s] = a.poses[5 * n + k] - a.oz;
             s_w[s] = tail ? 0.f : 0.5f * (a.weights ? a.weights[k] : 1.f);
         }
         __syncthreads();
