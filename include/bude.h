@@ -214,7 +214,11 @@ BUDE_API int bude_energies_batched(bude_deck* const* decks, const float* const* 
  * device, with that device current); make that first call before any stream
  * capture.  Every call shares the one array, so calls whose kernels overlap
  * on the GPU (different streams, or different threads) race and must be
- * serialised by the caller.  Arguments and results are as bude_energies.
+ * serialised by the caller.  The looked-up address is kept for the life of
+ * the process, so resetting or destroying a device's primary context
+ * (cudaDeviceReset) while the library is loaded is not supported: later
+ * calls on that device would use a stale address.  Arguments and results are
+ * as bude_energies.
  */
 BUDE_API int bude_energies_noalloc(bude_deck* deck, const float* poses, int64_t n,
                                    float* energies, const bude_options* opts, void* stream);

@@ -263,6 +263,18 @@ def _check_poses(poses: torch.Tensor, deck: Deck):
         raise ValueError("poses must be contiguous")
 
 
+def _check_out(out, n: int, deck: Deck, what: str = "out"):
+    """A caller-supplied output: the kernels write n float32 values through
+    its pointer, so it must be exactly that, on the deck's device."""
+    if not isinstance(out, torch.Tensor):
+        raise ValueError(f"{what} must be a torch tensor")
+    if out.shape != (n,) or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous float32 [{n}] tensor, "
+                         f"got {out.dtype} {tuple(out.shape)}")
+    if out.device != deck.device:
+        raise ValueError(f"{what} on {out.device}, deck on {deck.device}")
+
+
 def energies(deck: Deck, poses: torch.Tensor, out: torch.Tensor | None = None,
              opts=None, stream=None, **kw) -> torch.Tensor:
     """Per-pose energies (float32 [n]) of device poses [6, n]."""
@@ -270,8 +282,8 @@ def energies(deck: Deck, poses: torch.Tensor, out: torch.Tensor | None = None,
     n = poses.shape[1]
     if out is None:
         out = torch.empty(n, dtype=torch.float32, device=poses.device)
-    elif out.shape != (n,) or out.dtype != torch.float32 or not out.is_contiguous():
-        raise ValueError("out must be a contiguous float32 [n] tensor")
+    else:
+        _check_out(out, n, deck)
     o = _opts(opts, **kw)
     rc = load().bude_energies(deck.handle, ctypes.c_void_p(poses.data_ptr()), n,
                               ctypes.c_void_p(out.data_ptr()), ctypes.byref(o),
@@ -311,8 +323,7 @@ def energies_noalloc(deck: Deck, poses: torch.Tensor, out: torch.Tensor,
     kernel's scratch in the library's fixed device array (no allocation)."""
     _check_poses(poses, deck)
     n = poses.shape[1]
-    if out.shape != (n,) or out.dtype != torch.float32 or not out.is_contiguous():
-        raise ValueError("out must be a contiguous float32 [n] tensor")
+    _check_out(out, n, deck)
     o = _opts(opts, **kw)
     rc = load().bude_energies_noalloc(deck.handle, ctypes.c_void_p(poses.data_ptr()), n,
                                       ctypes.c_void_p(out.data_ptr()), ctypes.byref(o),
@@ -330,6 +341,12 @@ def energies_batched(decks, poses, outs=None, opts=None, stream=None, **kw):
         _check_poses(p, d)
     if outs is None:
         outs = [torch.empty(p.shape[1], dtype=torch.float32, device=p.device) for p in poses]
+    else:
+        outs = list(outs)
+        if len(outs) != m:
+            raise ValueError(f"{len(outs)} outputs for {m} decks")
+        for i, (d, p, o) in enumerate(zip(decks, poses, outs)):
+            _check_out(o, p.shape[1], d, f"outs[{i}]")
     VP = ctypes.c_void_p * m
     hd = VP(*[d.handle.value for d in decks])
     hp = VP(*[p.data_ptr() for p in poses])
@@ -366,6 +383,8 @@ def refine_device(deck: Deck, poses: torch.Tensor, steps: int = 10, step0: float
     n = poses.shape[1]
     if energies is None:
         energies = torch.empty(n, dtype=torch.float32, device=poses.device)
+    else:
+        _check_out(energies, n, deck, "energies")
     o = _opts(opts, **kw)
     rc = load().bude_refine(deck.handle, ctypes.c_void_p(poses.data_ptr()), n, int(steps),
                             float(step0), ctypes.c_void_p(energies.data_ptr()), ctypes.byref(o),
@@ -527,18 +546,3 @@ class PoseEnergy(torch.autograd.Function):
         (G,) = ctx.saved_tensors
         return G * grad_out.unsqueeze(0), None, None
 
-
-def refine(deck: Deck, poses: torch.Tensor, steps: int = 10, lr: float = 1e-3, opts=None):
-    """Plain gradient descent on the poses; returns (poses, energy history)."""
-    p = poses.detach().clone().requires_grad_(True)
-    hist = []
-    for _ in range(steps):
-        E = PoseEnergy.apply(p, deck, opts)
-        hist.append(E.detach().clone())
-        E.sum().backward()
-        with torch.no_grad():
-            p -= lr * p.grad
-            p.grad = None
-    with torch.no_grad():
-        hist.append(energies(deck, p.detach().contiguous(), opts=opts))
-    return p.detach(), hist

@@ -164,3 +164,75 @@ def test_he_lattice_is_seeded_and_symmetric():
     assert s["geom"].shape == (27, 3)
     np.testing.assert_array_equal(s["dens"], s["dens"].T)
     assert np.all(np.diff(s["xpnt"]) < 0)   # exponents sorted, largest first
+
+
+# --- caller-supplied outputs are checked before anything is launched --------
+#
+# The kernels write n float32 values through each output pointer, so a short,
+# mistyped, strided or host-side output (or a missing one in a batch) must be
+# refused by the binding.  A stub deck on the "meta" device stands in for a
+# GPU deck: every check below raises before the library is reached.
+
+class _StubDeck:
+    device = __import__("torch").device("meta")
+    n_lig, n_pro, n_types, n_rows = 4, 10, 3, 2
+
+    @property
+    def handle(self):
+        raise AssertionError("the library was reached")
+
+
+def _meta(*shape, dtype=None):
+    import torch
+    return torch.empty(*shape, dtype=dtype or torch.float32, device="meta")
+
+
+@pytest.mark.parametrize("bad", ["short", "long", "dtype", "strided", "cpu", "2d"])
+def test_bad_out_is_refused_before_any_launch(bad):
+    import torch
+    deck, P = _StubDeck(), _meta(6, 8)
+    out = {"short": _meta(7), "long": _meta(9), "dtype": _meta(8, dtype=torch.float64),
+           "strided": _meta(16)[::2], "cpu": torch.empty(8), "2d": _meta(8, 1)}[bad]
+    for call in (lambda: bude.energies(deck, P, out=out),
+                 lambda: bude.energies_noalloc(deck, P, out),
+                 lambda: bude.refine_device(deck, P, energies=out)):
+        with pytest.raises(ValueError):
+            call()
+
+
+def test_batched_outputs_are_checked_per_deck():
+    import torch
+    decks = [_StubDeck(), _StubDeck()]
+    poses = [_meta(6, 8), _meta(6, 5)]
+    with pytest.raises(ValueError, match="outputs for 2 decks"):
+        bude.energies_batched(decks, poses, outs=[_meta(8)])
+    with pytest.raises(ValueError, match="outs\\[1\\]"):
+        bude.energies_batched(decks, poses, outs=[_meta(8), _meta(8)])
+    with pytest.raises(ValueError, match="outs\\[0\\]"):
+        bude.energies_batched(decks, poses, outs=[torch.empty(8), _meta(5)])
+    with pytest.raises(ValueError, match="outs\\[1\\]"):
+        bude.energies_batched(decks, poses, outs=[_meta(8), _meta(5, dtype=torch.float16)])
+
+
+def test_bench_summary_is_compact_and_last(bench):
+    """The bench line ends with a rounded summary short enough that a reader
+    keeping only the last 1500 characters of the line still sees all of it."""
+    import json
+    row = {"poses_per_s": 1.2345678e7, "frac_fp32_peak": 0.86912345, "scaled_err_max": 1.5e-6}
+    line = {"value": 13636442.36, "ms_per_step": 4.806123, "e2e": {"value": 1.353e7},
+            "config": {"variant": "fast"},
+            "roofline": {"frac": 0.8687, "executed_frac": 0.61523},
+            "variants": {v: dict(row) for v in ("ieee", "fast", "comp", "fp64")},
+            "batched": {"batched_ms": 24.58, "plain_ms": 27.6, "speedup": 1.1229,
+                        "batched_eq3_frac_fp32_peak": 0.8351, "plain_tuned_decks": 63,
+                        "scaled_err_max_batched": 1.234e-6, "scaled_err_max_plain": 2.2e-6},
+            "adjoint": {"ms": 2.19, "executed": {"frac_fp32_peak": 0.5851}},
+            "refine": {"ms": 24.1}, "param_grad": {"ms": 2.26},
+            "cull": {"ms": 2.91, "bit_identical_to_unculled": True},
+            "cpu_baseline": {"value": 19125.7}}
+    line["summary"] = bench.summary(line)
+    text = json.dumps(line)
+    tail = text[-1500:]
+    assert json.dumps(line["summary"]) in tail
+    assert line["summary"]["batched"]["speedup"] == 1.123
+    assert line["summary"]["headline"]["eq3_frac"] == 0.8687

@@ -7,10 +7,14 @@ with its scratch in the library's fixed device array.  This file is named to
 be collected last, so that a run stopping at the first failure has already
 run every other test; it passes alone in a fresh process and after the
 others.
+
+The two entry points run the same kernel in the same launch shape with the
+same fixed-order reductions, so their results must be identical bit for bit:
+any difference would mean the shared array leaked one call's partial sums
+or tickets into another.
 """
 import ctypes
 
-import numpy as np
 import pytest
 import torch
 
@@ -19,7 +23,9 @@ from paper_2509_21039_gb300 import bude, synth
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
-GATE_IEEE = 1e-5   # the FP32 IEEE parity gate of the other GPU tests
+# the array's capacity (include/bude.h): partial sums and tickets
+STATIC_PARTIAL_DOUBLES = 512 * 1024
+STATIC_TICKETS = 16 * 1024
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -47,12 +53,11 @@ def test_noalloc_matches_energies_twice_in_a_row(variant, ppwi):
     deck = bude.Deck(D, device=DEV)
     P = torch.from_numpy(D["poses"]).to(DEV)
     opts = bude.LaunchOptions(variant=variant, ppwi=ppwi, block=256)
-    ref = bude.energies(deck, P, opts=opts).cpu().numpy().astype(np.float64)
+    ref = bude.energies(deck, P, opts=opts).clone()
     out = torch.full((P.shape[1],), float("nan"), device=DEV)
     for _ in range(2):   # the second call reuses the array the first one left behind
-        E = _call_noalloc(deck, P, out, opts).cpu().numpy().astype(np.float64)
-        err = np.abs(E - ref) / np.maximum(np.abs(ref), 1.0)
-        assert err.max() <= GATE_IEEE, err.max()
+        E = _call_noalloc(deck, P, out, opts)
+        assert torch.equal(E, ref)
         out.fill_(float("nan"))
 
 
@@ -60,11 +65,12 @@ def test_noalloc_small_and_full_size_decks():
     for D in (synth.make_deck(132, 5, 60, 7, 33), synth.make_deck(1, **synth.FULL)):
         deck = bude.Deck(D, device=DEV)
         P = torch.from_numpy(D["poses"]).to(DEV)
-        ref = bude.energies(deck, P).cpu().numpy().astype(np.float64)
+        ref = bude.energies(deck, P).clone()
         out = torch.empty(P.shape[1], device=DEV)
         for _ in range(2):
-            E = bude.energies_noalloc(deck, P, out).cpu().numpy().astype(np.float64)
-            assert (np.abs(E - ref) / np.maximum(np.abs(ref), 1.0)).max() <= GATE_IEEE
+            E = bude.energies_noalloc(deck, P, out)
+            torch.cuda.synchronize()
+            assert torch.equal(E, ref)
 
 
 def test_noalloc_rejects_more_poses_than_its_scratch_holds():
@@ -80,6 +86,31 @@ def test_noalloc_rejects_more_poses_than_its_scratch_holds():
     # the library is still usable afterwards
     small = torch.from_numpy(D["poses"]).to(DEV)
     o2 = torch.empty(small.shape[1], device=DEV)
-    ref = bude.energies(deck, small).cpu().numpy()
-    np.testing.assert_allclose(bude.energies_noalloc(deck, small, o2).cpu().numpy(), ref,
-                               rtol=1e-5, atol=1e-5)
+    ref = bude.energies(deck, small).clone()
+    assert torch.equal(bude.energies_noalloc(deck, small, o2), ref)
+
+
+def test_noalloc_partial_sum_bound_alone():
+    """A call whose tickets fit but whose partial sums do not: at 16 poses
+    per lane and one CTA per SM the grid has one CTA per SM, and a call needs
+    (CTAs + tiles) x 512 partial sums.  The largest pose count that fits
+    exactly fills the array and must match bude_energies; one pose more needs
+    one more tile, which no longer fits."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    opts = dict(variant="ieee", ppwi=16, block=384, ctas_per_sm=1)
+    slots = STATIC_PARTIAL_DOUBLES // (32 * 16)
+    n_fit = (slots - sms) * 32 * 16
+    assert n_fit // 512 < STATIC_TICKETS and (n_fit + 1 + 511) // 512 < STATIC_TICKETS
+    D = synth.make_deck(134, 4, 40, 5, n_fit + 1)
+    deck = bude.Deck(D, device=DEV)
+    P_all = torch.from_numpy(D["poses"]).to(DEV)
+    out = torch.empty(n_fit + 1, device=DEV)
+    with pytest.raises(bude.BudeError) as e:
+        bude.energies_noalloc(deck, P_all, out, **opts)
+    assert e.value.code == bude.ERR_UNSUPPORTED
+    assert "partial sums" in str(e.value)
+    P = P_all[:, :n_fit].contiguous()
+    ref = bude.energies(deck, P, **opts).clone()
+    E = bude.energies_noalloc(deck, P, out[:n_fit], **opts)
+    torch.cuda.synchronize()
+    assert torch.equal(E, ref)
