@@ -37,32 +37,31 @@ SM_MAX_MHZ = 2070.0
 FP32_LANES_PER_SM = 128
 
 
-# DRAM traffic of one full-size FAST launch, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, mean of 9 launches; see
-# profiles/pose_kernel_fast_64x2672x65536_launches.md).  Reported only
-# while the kernel source and the launch shape are the ones that were
-# measured.
-MEASURED_TRAFFIC = {"kernel_sha256_16": "41d527a5f5b7247c", "variant": "fast", "ppwi": 16,
-                    "block": 384, "bytes": 1863367.0}
+# DRAM traffic of one full-size FAST launch, from one ncu capture of this
+# kernel and shape (dram__bytes_read.sum + dram__bytes_write.sum, mean of 9
+# launches).  Reported only while the kernel source and the launch shape are
+# the ones that were measured; otherwise the line says why it is missing.
+MEASURED_TRAFFIC = {"kernel_sha256_16": "4ff7fdb82b2ca857", "variant": "fast", "ppwi": 16,
+                    "block": 384, "bytes": 1947250.0}
 
 # FP32 FLOPs the kernel executes per pose-pair on the full deck, from ncu's
 # per-opcode thread-instruction counters of the same launch (FADD, FMUL 1;
 # FFMA, FADD2, FMUL2 2; FFMA2 4), per variant, for the kernel source with
 # this hash.  Fewer than Eq. 3's 30: zero desolvation runs are skipped, and
-# FAST rearranges the squared distance and the steric term.
-MEASURED_EXECUTED = {"kernel_sha256_16": "41d527a5f5b7247c",
-                     "flop_per_pair": {"fast": 21.25, "ieee": 29.25, "comp": 29.24}}
+# FAST takes the steric term as sign(H) z^2 with one fewer operation.
+MEASURED_EXECUTED = {"kernel_sha256_16": "4ff7fdb82b2ca857",
+                     "flop_per_pair": {"fast": 22.24, "ieee": 29.25, "comp": 29.24}}
 
 # The same count for the FAST adjoint (energies and pose gradients) at P = 8
 # on the 64 x 2672 x 16384 workload: the force and torque sums add the
 # reciprocal root's products and three FFMA2 per pose pair to the energy work.
-MEASURED_EXECUTED_ADJOINT = {"kernel_sha256_16": "41d527a5f5b7247c", "variant": "fast", "ppwi": 8,
+MEASURED_EXECUTED_ADJOINT = {"kernel_sha256_16": "4ff7fdb82b2ca857", "variant": "fast", "ppwi": 8,
                              "flop_per_pair": 36.77}
 
 # The same count for the FAST forcefield-gradient kernel (param_kernel) at
 # P = 8 on the 64 x 2672 x 16384 workload; the hash covers both of its
 # source files.
-MEASURED_EXECUTED_PARAM = {"kernel_sha256_16": "66e50885d6bb26e2", "variant": "fast", "ppwi": 8,
+MEASURED_EXECUTED_PARAM = {"kernel_sha256_16": "dbae48a509055bc8", "variant": "fast", "ppwi": 8,
                            "flop_per_pair": 39.12}
 
 
@@ -92,6 +91,17 @@ def measured_executed(variant):
     return m["flop_per_pair"].get(variant)
 
 
+def executed_source(variant):
+    """Where roofline.executed_* come from, or why they are absent."""
+    sha = kernel_sha()
+    if sha != MEASURED_EXECUTED["kernel_sha256_16"]:
+        return (f"absent: the ncu opcode counts were taken on kernel source "
+                f"{MEASURED_EXECUTED['kernel_sha256_16']}, this is {sha}")
+    if variant not in MEASURED_EXECUTED["flop_per_pair"]:
+        return f"absent: no opcode count for variant {variant}"
+    return f"ncu opcode counters of kernel source {sha}, full deck"
+
+
 def measured_traffic(variant, ppwi, block, n_poses):
     sha = kernel_sha()
     if sha is None:
@@ -101,6 +111,19 @@ def measured_traffic(variant, ppwi, block, n_poses):
                                                  m["block"], FULL["n_poses"]):
         return None
     return m["bytes"]
+
+
+def traffic_source(variant, ppwi, block, n_poses):
+    """Where roofline.traffic comes from, or why it is null."""
+    m = MEASURED_TRAFFIC
+    sha = kernel_sha()
+    if sha != m["kernel_sha256_16"]:
+        return (f"null: DRAM bytes were captured on kernel source {m['kernel_sha256_16']}, "
+                f"this is {sha}")
+    if (variant, ppwi, block, n_poses) != (m["variant"], m["ppwi"], m["block"], FULL["n_poses"]):
+        return (f"null: DRAM bytes were captured for {m['variant']} P={m['ppwi']} "
+                f"block={m['block']} on {FULL['n_poses']} poses")
+    return f"ncu dram__bytes_read.sum + dram__bytes_write.sum of kernel source {sha}"
 
 
 def eq3_flops(n_lig, n_pro, n_poses, ppwi):
@@ -236,14 +259,23 @@ def batched_vs_plain(bude, synth, tune, dev, timed, variant="fast", count=64, se
                                 ctas_per_sm=e["ctas_per_sm"], tile=e["tile"])
     else:
         ob = bude.default_options(variant)
-    op = bude.default_options(variant)
+    # each plain launch takes the shape tuned for its own workload bucket
+    # (the default when the table has none for that bucket)
+    tbl = tune.load_table()
+    ops = []
+    for d in decks_np:
+        o = tune.lookup(variant, len(d["lig_type"]), len(d["pro_type"]), d["poses"].shape[1],
+                        table=tbl)
+        ops.append(o)
+    plain_tuned = sum(o is not None for o in ops)
+    ops = [o if o is not None else bude.default_options(variant) for o in ops]
 
     def run_batched():
         bude.energies_batched(decks, poses, outs_b, opts=ob)
 
     def run_plain():
         n = 0
-        for d, p, o in zip(decks, poses, outs_p):
+        for d, p, o, op in zip(decks, poses, outs_p, ops):
             bude.energies(d, p, out=o, opts=op)
             n += bude.launch_count()
         plain_launches[0] = n
@@ -269,6 +301,13 @@ def batched_vs_plain(bude, synth, tune, dev, timed, variant="fast", count=64, se
     pairs = sum(len(d["lig_type"]) * len(d["pro_type"]) * d["poses"].shape[1] for d in decks_np)
     n = sum(d["poses"].shape[1] for d in decks_np)
     diff = max(float(((a - b).abs() / b.abs().clamp_min(1.0)).max()) for a, b in zip(outs_b, outs_p))
+    # energies of both arms at 16 poses per deck (the last one included), for
+    # the oracle comparison of the CPU-baseline leg
+    samples = []
+    for d, a, b in zip(decks_np, outs_b, outs_p):
+        m = d["poses"].shape[1]
+        idx = np.unique(np.linspace(0, m - 1, 16).round().astype(np.int64))
+        samples.append((idx, a.cpu().numpy()[idx], b.cpu().numpy()[idx]))
     for d in decks:
         d.close()
     tb, tp = statistics.mean(ms_b), statistics.mean(ms_p)
@@ -285,10 +324,14 @@ def batched_vs_plain(bude, synth, tune, dev, timed, variant="fast", count=64, se
             "batched_poses_per_s": n / (tb / 1e3), "plain_poses_per_s": n / (tp / 1e3),
             "batched_launches": lb // 10, "plain_launches": plain_launches[0],
             "batched_opts": {"ppwi": ob.ppwi, "block": ob.block, "ctas_per_sm": ob.ctas_per_sm},
+            "plain_opts": f"tuned per workload bucket for {plain_tuned} of {count} decks, "
+                          f"the library default for the rest",
+            "plain_tuned_decks": plain_tuned,
             "max_rel_diff_batched_vs_plain": diff,
             "batched_cull_ms": statistics.mean(ms_c), "batched_cull_bit_identical": cull_same,
             "batched_cull_opts": {"ppwi": ob_c.ppwi, "block": ob_c.block,
-                                  "ctas_per_sm": ob_c.ctas_per_sm}}
+                                  "ctas_per_sm": ob_c.ctas_per_sm},
+            "_samples": samples, "_decks": decks_np}
 
 
 def adjoint_throughput(bude, synth, tune, dev, timed, variant="fast"):
@@ -508,6 +551,77 @@ def hartree_fock(bude, synth, dev, timed, sizes=(64, 128, 256), variants=("ieee"
     return out
 
 
+def workload_name(shard, shape, world):
+    """config.workload for a shard mode."""
+    deck = (f"{shape['n_lig']} lig x {shape['n_pro']} pro x {shape['n_poses']} poses, "
+            f"34 types")
+    if shard == "decks":
+        return f"deck {deck}, seed 1+rank (one deck per GPU)"
+    if shard == "poses":
+        return f"deck {deck}, seed 1, poses split over {world} GPUs"
+    return ("64 decks, log-uniform lig 8-128, pro 500-5000, poses 1024-65536, 34 types, "
+            f"seed 3, split over {world} GPUs")
+
+
+def batched_oracle_errors(decks_np, samples):
+    """Largest scaled error |E - E_ref| / max(A_ref, 1) of the batched and the
+    plain arm over the sampled poses of every deck (the oracle's energies and
+    absolute-term sums at those poses)."""
+    import oracle
+    eb = ep = 0.0
+    for d, (idx, a, b) in zip(decks_np, samples):
+        ref, A = oracle.energies(d, np.ascontiguousarray(d["poses"][:, idx]), n_threads=-1,
+                                 with_abs=True)
+        sc = np.maximum(A, 1.0)
+        eb = max(eb, float((np.abs(a.astype(np.float64) - ref) / sc).max()))
+        ep = max(ep, float((np.abs(b.astype(np.float64) - ref) / sc).max()))
+    return eb, ep
+
+
+def _r(x, digits=4):
+    """x rounded to a few significant digits (None stays None)."""
+    if x is None:
+        return None
+    if isinstance(x, bool) or not isinstance(x, (int, float)):
+        return x
+    return float(f"{x:.{digits}g}")
+
+
+def summary(line):
+    """The figures a reader looks for first, rounded, as the line's last key
+    (a consumer that keeps only the end of the line still sees them)."""
+    rf = line["roofline"]
+    out = {"headline": {"variant": line["config"]["variant"], "poses_s": _r(line["value"]),
+                        "ms": _r(line["ms_per_step"]), "eq3_frac": _r(rf["frac"]),
+                        "exec_frac": _r(rf.get("executed_frac")),
+                        "e2e_poses_s": _r(line["e2e"]["value"])}}
+    for v, row in line.get("variants", {}).items():
+        out[v] = {"poses_s": _r(row["poses_per_s"]), "eq3_frac": _r(row["frac_fp32_peak"]),
+                  "err": _r(row["scaled_err_max"], 2)}
+    b = line.get("batched")
+    if b:
+        out["batched"] = {"ms": _r(b["batched_ms"]), "plain_ms": _r(b["plain_ms"]),
+                          "speedup": _r(b["speedup"]),
+                          "eq3_frac": _r(b["batched_eq3_frac_fp32_peak"]),
+                          "plain_tuned": f"{b['plain_tuned_decks']}/64",
+                          "err_b": _r(b.get("scaled_err_max_batched"), 2),
+                          "err_p": _r(b.get("scaled_err_max_plain"), 2)}
+    a = line.get("adjoint")
+    if a:
+        out["adjoint"] = {"ms": _r(a["ms"]),
+                          "exec_frac": _r((a.get("executed") or {}).get("frac_fp32_peak"))}
+    if line.get("refine"):
+        out["refine_ms"] = _r(line["refine"]["ms"])
+    if line.get("param_grad"):
+        out["param_grad_ms"] = _r(line["param_grad"]["ms"])
+    if line.get("cull"):
+        out["cull"] = {"ms": _r(line["cull"]["ms"]),
+                       "same": line["cull"]["bit_identical_to_unculled"]}
+    if line.get("cpu_baseline"):
+        out["oracle_poses_s"] = _r(line["cpu_baseline"]["value"])
+    return out
+
+
 def reference_arm(args):
     """The FP64 oracle as it stands, timed on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -577,6 +691,10 @@ def main():
                     help="only the pose-gradient (adjoint) extra (profiling)")
     ap.add_argument("--hf-only", type=int, default=0, metavar="ATOMS",
                     help="only the FP32-integral Fock build on this many atoms (profiling)")
+    ap.add_argument("--shard", default="decks", choices=["decks", "poses", "batch"],
+                    help="decks: one deck per rank (weak scaling, the default); poses: one "
+                         "full-size deck's poses split over the ranks; batch: the 64-deck "
+                         "uneven batch split over the ranks (both strong scaling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -599,12 +717,23 @@ def main():
     shape = dict(SMALL if args.small else FULL)
     if args.poses:
         shape["n_poses"] = args.poses
-    # each rank docks its own deck (independent problems: weak scaling)
-    D = synth.make_deck(bdist.rank_seed(1, rank), **shape)
-    deck = bude.Deck(D, device=dev)
-    poses = torch.from_numpy(D["poses"]).to(dev)
-    n = poses.shape[1]
-    out = torch.empty(n, dtype=torch.float32, device=dev)
+    # The work of this rank (dist.shard_pieces; no data-path collective):
+    #   decks  its own deck, seed 1 + rank (independent problems, weak scaling)
+    #   poses  a contiguous slice of the poses of the seed-1 deck (strong)
+    #   batch  its pieces of the 64-deck uneven batch (strong)
+    shard = args.shard
+    batch_np = None
+    if shard == "batch":
+        batch_np = synth.make_batched(3, 64)
+        shapes_b = [(len(d["lig_type"]), len(d["pro_type"]), d["poses"].shape[1])
+                    for d in batch_np]
+        pieces, total_units, scaling = bdist.shard_pieces("batch", rank, world,
+                                                          batch_shapes=shapes_b)
+        total_alg = sum(algorithmic_flops(*sh) for sh in shapes_b)
+    else:
+        pieces, total_units, scaling = bdist.shard_pieces(shard, rank, world,
+                                                          n_poses=shape["n_poses"])
+        total_alg = algorithmic_flops(shape["n_lig"], shape["n_pro"], total_units)
     flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     # launch shapes found by the autotuner on GB300 (tuned.json), else defaults
@@ -612,8 +741,36 @@ def main():
     resolved = bude.default_options(args.variant)
     opts = resolved
 
-    def step():
-        bude.energies(deck, poses, out=out, opts=opts)
+    if shard != "batch":
+        (_, lo, hi), = pieces
+        D = synth.make_deck(bdist.rank_seed(1, rank) if shard == "decks" else 1, **shape)
+        if (lo, hi) != (0, shape["n_poses"]):
+            D["poses"] = np.ascontiguousarray(D["poses"][:, lo:hi])
+        deck = bude.Deck(D, device=dev)
+        poses = torch.from_numpy(D["poses"]).to(dev)
+        n = poses.shape[1]
+        out = torch.empty(n, dtype=torch.float32, device=dev)
+
+        def step():
+            bude.energies(deck, poses, out=out, opts=opts)
+    else:
+        # one batched launch over this rank's pieces, in the batch's tuned shape
+        D = None
+        e = tune.load_table().get(tune.key(args.variant, "n64", "batched"))
+        bopts = (bude.LaunchOptions(variant=args.variant, ppwi=e["ppwi"], block=e["block"],
+                                    ctas_per_sm=e["ctas_per_sm"], tile=e["tile"])
+                 if e else opts)
+        deck_of = {i: bude.Deck(batch_np[i], device=dev) for i in sorted({p[0] for p in pieces})}
+        b_decks = [deck_of[i] for i, _, _ in pieces]
+        b_host = [torch.from_numpy(np.ascontiguousarray(batch_np[i]["poses"][:, a:b]))
+                  for i, a, b in pieces]
+        b_poses = [h.to(dev) for h in b_host]
+        b_outs = [torch.empty(h.shape[1], dtype=torch.float32, device=dev) for h in b_host]
+        n = sum(h.shape[1] for h in b_host)
+
+        def step():
+            if b_decks:
+                bude.energies_batched(b_decks, b_poses, b_outs, opts=bopts)
 
     def timed(fn, steps, warmup):
         for _ in range(warmup):
@@ -668,15 +825,32 @@ def main():
     with ClockSampler(local, args.clocks_csv) as clk:
         ms, launches = timed(step, args.steps, args.warmup)
     ms_mean = bdist.max_over_ranks(statistics.mean(ms), dev)
-    value = bdist.aggregate_rate(n, ms_mean, world)
+    value = total_units / (ms_mean / 1e3)
 
-    # end to end through the C ABI's host-buffer call: pinned host poses in,
-    # host energies out, both copies made by the library on the stream
-    host_poses = torch.from_numpy(D["poses"]).pin_memory()
-    host_out = torch.empty(n, dtype=torch.float32).pin_memory()
+    if shard != "batch":
+        # end to end through the C ABI's host-buffer call: pinned host poses in,
+        # host energies out, both copies made by the library on the stream
+        host_poses = torch.from_numpy(D["poses"]).pin_memory()
+        host_out = torch.empty(n, dtype=torch.float32).pin_memory()
+        h2d, d2h = host_poses.numel() * 4, host_out.numel() * 4
 
-    def e2e_step():
-        bude.energies_host(deck, host_poses, out=host_out, opts=opts)
+        def e2e_step():
+            bude.energies_host(deck, host_poses, out=host_out, opts=opts)
+    else:
+        # the batched call a user makes from host buffers: pinned poses copied
+        # in, one batched launch, energies copied back
+        pin_in = [h.pin_memory() for h in b_host]
+        pin_out = [torch.empty(h.shape[1], dtype=torch.float32).pin_memory() for h in b_host]
+        h2d = sum(h.numel() * 4 for h in pin_in)
+        d2h = sum(h.numel() * 4 for h in pin_out)
+
+        def e2e_step():
+            for h, d in zip(pin_in, b_poses):
+                d.copy_(h, non_blocking=True)
+            step()
+            for o, h in zip(b_outs, pin_out):
+                h.copy_(o, non_blocking=True)
+            stream.synchronize()
 
     e2e_ms, _ = timed(e2e_step, max(3, args.steps // 2), 2)
     e2e_mean = bdist.max_over_ranks(statistics.mean(e2e_ms), dev)
@@ -690,25 +864,43 @@ def main():
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     clocks = clk.summary()
     peak_max = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    alg = algorithmic_flops(shape["n_lig"], shape["n_pro"], n)
-    achieved = alg / (ms_mean / 1e3) / 1e12 / world  # per GPU, per launch
+    # per GPU: the FLOPs of all ranks' launches over the slowest rank's time,
+    # shared out over the GPUs
+    achieved = total_alg / world / (ms_mean / 1e3) / 1e12
     ppwi = resolved.ppwi
+    if shard == "batch":
+        ppwi = bopts.ppwi
+    if shard == "batch":
+        sh = [(len(batch_np[i]["lig_type"]), len(batch_np[i]["pro_type"]), b - a)
+              for i, a, b in pieces]
+        kernel = f"pose_kernel<{args.variant}, P={ppwi}>, one batched launch"
+        block = bopts.block
+    else:
+        sh = [(shape["n_lig"], shape["n_pro"], n)]
+        kernel = f"pose_kernel<{args.variant}, P={ppwi}>"
+        block = resolved.block
+    alg_rank = sum(algorithmic_flops(*x) for x in sh)
     roofline = {
         "bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
         "frac": achieved / peak_max,
-        "traffic": measured_traffic(args.variant, ppwi, resolved.block, n),
-        "algorithmic_bytes": int(n * 28 + 4 * (shape["n_pro"] + shape["n_lig"]) * 4),
-        "kernel": f"pose_kernel<{args.variant}, P={ppwi}>",
-        "flops_per_launch": alg,
+        "traffic": measured_traffic(args.variant, ppwi, block, n) if shard != "batch" else None,
+        "traffic_source": (traffic_source(args.variant, ppwi, block, n) if shard != "batch"
+                           else "null: DRAM bytes were captured for the single-deck launch"),
+        "algorithmic_bytes": int(sum(x[2] * 28 + 4 * (x[0] + x[1]) * 4 for x in sh)),
+        "kernel": kernel,
+        "flops_per_launch": alg_rank,
         "flop_count": "Eq. 3 in the many-poses limit: 28 + nlig (18 + 30 npro) per pose",
         "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz",
-        "eq3_tflops_at_ppwi": eq3_flops(shape["n_lig"], shape["n_pro"], n, ppwi) / (ms_mean / 1e3) / 1e12,
+        "eq3_tflops_at_ppwi": sum(eq3_flops(*x, ppwi) for x in sh) / (ms_mean / 1e3) / 1e12,
     }
     xf = measured_executed(args.variant)
-    if xf is not None:
-        # FLOPs the kernel executes (ncu opcode counters), not Eq. 3's count
+    roofline["executed_source"] = executed_source(args.variant)
+    if xf is not None and shard != "batch":
+        # FLOPs the kernel executes (ncu opcode counters), not Eq. 3's count,
+        # per GPU as achieved above
+        pairs = shape["n_lig"] * shape["n_pro"] * total_units / world
         roofline["executed_flop_per_pair"] = xf
-        roofline["executed_tflops"] = xf * shape["n_lig"] * shape["n_pro"] * n / (ms_mean / 1e3) / 1e12
+        roofline["executed_tflops"] = xf * pairs / (ms_mean / 1e3) / 1e12
         roofline["executed_frac"] = roofline["executed_tflops"] / peak_max
     if clocks:
         clk_peak = sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12
@@ -718,36 +910,44 @@ def main():
         "metric": METRIC, "value": value, "unit": "poses/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mean,
         "ms_per_step_median": statistics.median(ms), "ms_per_step_best": min(ms),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": scaling, "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": (f"deck {shape['n_lig']} lig x {shape['n_pro']} pro x "
-                                f"{shape['n_poses']} poses, 34 types, seed 1+rank"),
-                   "variant": args.variant, "ppwi": ppwi, "block": resolved.block,
-                   "ctas_per_sm": resolved.ctas_per_sm,
+        "config": {"workload": workload_name(shard, shape, world),
+                   "variant": args.variant, "ppwi": ppwi, "block": block,
+                   "ctas_per_sm": (bopts if shard == "batch" else resolved).ctas_per_sm,
                    "l2": f"flushed ({args.flush_mb} MiB write) before every timed step",
-                   "parallelism": f"independent decks per GPU x{world}"},
+                   "parallelism": {"decks": f"independent decks per GPU x{world}",
+                                   "poses": f"one deck's poses split over {world} GPUs",
+                                   "batch": f"64-deck batch split over {world} GPUs"}[shard],
+                   "shard": shard},
         "gpu_launches": int(launches),
-        "e2e": {"value": bdist.aggregate_rate(n, e2e_mean, world), "unit": "poses/s",
-                "h2d_bytes_per_step": int(host_poses.numel() * 4),
-                "d2h_bytes_per_step": int(host_out.numel() * 4)},
+        "e2e": {"value": total_units / (e2e_mean / 1e3), "unit": "poses/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "roofline": roofline,
         "clocks": clocks,
     }
 
+    batched_private = {}
+    if shard != "decks":
+        # the extras and the variant table belong to the single-deck workload
+        args.no_extras = True
+        if not args.no_cpu_baseline:
+            D = synth.make_deck(1, **FULL)
     if not args.no_extras:
-        line["cull"] = cull_throughput(bude, tune, deck, poses, out, ms_mean, timed)
-        line["batched"] = batched_vs_plain(bude, synth, tune, dev, timed)
-        line["adjoint"] = adjoint_throughput(bude, synth, tune, dev, timed)
-        line["refine"] = refine_throughput(bude, synth, tune, dev, timed)
-        line["param_grad"] = param_grad_throughput(bude, synth, tune, dev, timed)
         line["hbm_calibration"] = hbm_calibration(bude, dev, timed,
                                                   peaks.get("hbm_gbs", 6800.0))
         line["hartree_fock"] = hartree_fock(bude, synth, dev, timed)
+        line["cull"] = cull_throughput(bude, tune, deck, poses, out, ms_mean, timed)
+        line["batched"] = batched_vs_plain(bude, synth, tune, dev, timed)
+        batched_private = {k: line["batched"].pop(k) for k in ("_samples", "_decks")}
+        line["adjoint"] = adjoint_throughput(bude, synth, tune, dev, timed)
+        line["refine"] = refine_throughput(bude, synth, tune, dev, timed)
+        line["param_grad"] = param_grad_throughput(bude, synth, tune, dev, timed)
 
     # CPU-baseline leg: the FP64 oracle on a bounded sample of the same poses.
     # Its sample energies also give each variant's error on that sample.
     if not args.no_cpu_baseline:
-        v, k, dt, cores, ref, A = cpu_baseline_leg(D, n)
+        v, k, dt, cores, ref, A = cpu_baseline_leg(D, D["poses"].shape[1])
         v1, k1 = cpu_single_thread(D)
         line["cpu_baseline"] = {"value": v, "unit": "poses/s", "cores": cores, "kind": "oracle",
                                 "sample": f"first {k} poses of the same deck, FP64, best of 3 "
@@ -775,7 +975,7 @@ def main():
                 rel = ab / np.maximum(np.abs(rf), 1e-30)
                 t = statistics.mean(vms) / 1e3
                 variants[vname] = {"poses_per_s": npos / t,
-                                   "frac_fp32_peak": (alg * npos / n) / t / 1e12 / peak_max,
+                                   "frac_fp32_peak": (alg_rank * npos / n) / t / 1e12 / peak_max,
                                    "scaled_err_max": float(err.max()),
                                    "abs_err_median": float(np.median(ab)),
                                    "abs_err_max": float(ab.max()),
@@ -789,6 +989,14 @@ def main():
                     variants[vname]["executed_frac"] = (xv * shape["n_lig"] * shape["n_pro"] * npos
                                                         / t / 1e12 / peak_max)
             line["variants"] = variants
+            if batched_private:
+                # both batched-comparison arms against the oracle at the sampled poses
+                eb, ep = batched_oracle_errors(batched_private["_decks"],
+                                               batched_private["_samples"])
+                line["batched"]["scaled_err_max_batched"] = eb
+                line["batched"]["scaled_err_max_plain"] = ep
+                line["batched"]["error_sample"] = "16 poses per deck (the last included), FP64 oracle"
+    line["summary"] = summary(line)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

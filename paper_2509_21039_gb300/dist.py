@@ -100,3 +100,34 @@ def split_and_partition(shapes, world_size: int) -> list[list[tuple[int, int, in
             piece_cost.append(float(deck_cost(nl, npro, hi - lo)))
     parts = lpt_partition(piece_cost, world_size)
     return [[pieces[i] for i in p] for p in parts]
+
+
+SHARD_MODES = ("decks", "poses", "batch")
+
+
+def shard_pieces(mode: str, rank: int, world_size: int, n_poses: int = 0, batch_shapes=None):
+    """The work one rank evaluates, as (pieces, total_units, scaling).
+
+    pieces are (deck, lo, hi) slices of a deck's poses:
+      "decks"  each rank docks its own deck (deck index = rank), all its poses:
+               independent problems, weak scaling;
+      "poses"  one deck (index 0) whose n_poses are cut into contiguous slices,
+               one per rank: strong scaling;
+      "batch"  a batch of uneven decks (batch_shapes: (n_lig, n_pro, n_poses)
+               per deck) split and assigned by split_and_partition: strong
+               scaling.
+    total_units is the number of poses all ranks evaluate together.  Every
+    rank computes the same assignment, so nothing is exchanged."""
+    if world_size < 1 or not 0 <= rank < world_size:
+        raise ValueError("bad rank or world size")
+    if mode == "decks":
+        return [(rank, 0, int(n_poses))], world_size * int(n_poses), "weak"
+    if mode == "poses":
+        lo, hi = shard_range(int(n_poses), rank, world_size)
+        return [(0, lo, hi)], int(n_poses), "strong"
+    if mode == "batch":
+        if not batch_shapes:
+            raise ValueError("batch mode needs the decks' shapes")
+        parts = split_and_partition(batch_shapes, world_size)
+        return parts[rank], sum(int(s[2]) for s in batch_shapes), "strong"
+    raise ValueError(f"unknown shard mode {mode!r}; one of {SHARD_MODES}")

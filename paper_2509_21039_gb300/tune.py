@@ -168,6 +168,33 @@ def tune_batched(decks, poses, variant: str, space=None, reps: int = 5, log=None
         decks, poses, outs, opts=o)), reps=reps, log=log, tag=f"batched {variant}")
 
 
+def tune_plain_group(decks, poses, variant: str, space=None, reps: int = 5, log=None):
+    """Fastest launch shape for plain bude_energies calls over several decks
+    of one workload bucket: each candidate is timed over one call per deck,
+    so the shape that wins is the best for the bucket as a whole."""
+    outs = [torch.empty(p.shape[1], dtype=torch.float32, device=p.device) for p in poses]
+
+    def run(o):
+        for d, p, out in zip(decks, poses, outs):
+            bude.energies(d, p, out=out, opts=o)
+
+    results = []
+    for o in candidates(variant, space):
+        try:
+            ms = time_call(lambda: run(o), reps)
+        except bude.BudeError as e:
+            if e.code != bude.ERR_UNSUPPORTED:
+                raise
+            continue
+        results.append((ms, o))
+        if log:
+            log(f"group {variant} P={o.ppwi:2d} block={o.block:4d} cps={o.ctas_per_sm}: "
+                f"{ms:.3f} ms")
+    results.sort(key=lambda r: r[0])
+    return _tile_stage(results, fn_of=lambda o: (lambda: run(o)), reps=reps, log=log,
+                       tag=f"group {variant}")
+
+
 def record(table: dict, k: str, ms: float, o) -> None:
     table[k] = {"ppwi": o.ppwi, "block": o.block, "ctas_per_sm": o.ctas_per_sm,
                 "tile": o.tile, "ms": round(ms, 4)}
@@ -219,6 +246,10 @@ def _workloads(which):
         yield "param", [synth.make_deck(4, **synth.GRAD)]
     if "batched" in which:
         yield "batched", synth.make_batched(3, 64)
+    if "batched_plain" in which:
+        # the plain launches the batched launch is compared with: one shape per
+        # workload bucket of the 64 decks
+        yield "batched_plain", synth.make_batched(3, 64)
 
 
 def main(argv=None):
@@ -252,6 +283,26 @@ def main(argv=None):
                 space = {"ppwi": [1, 2, 4], "block": [128, 192, 256, 384, 512],
                          "ctas_per_sm": [1, 2, 3], "tile": [0]}
             elif name == "full_fp64":
+                continue
+            if name == "batched_plain":
+                if v not in ("fast", "ieee"):
+                    continue
+                groups: dict = {}
+                for i, d in enumerate(decks_np):
+                    b = bucket(len(d["lig_type"]), len(d["pro_type"]), d["poses"].shape[1])
+                    groups.setdefault(b, []).append(i)
+                for b, idx in sorted(groups.items()):
+                    k = key(v, b)
+                    if k in table:
+                        continue   # tuned on its own workload already
+                    res = tune_plain_group([decks[i] for i in idx], [poses[i] for i in idx], v,
+                                           space, a.reps, log)
+                    if res:
+                        record(table, k, res[0][0], res[0][1])
+                        table[k]["decks"] = len(idx)
+                        print(f"{k}: {len(idx)} decks, P{res[0][1].ppwi}/b{res[0][1].block}/"
+                              f"c{res[0][1].ctas_per_sm}/t{res[0][1].tile}:{res[0][0]:.3f}",
+                              flush=True)
                 continue
             if name == "batched":
                 if v not in ("fast", "ieee"):

@@ -210,3 +210,100 @@ def test_split_and_partition_balances_the_batched_workload():
     # one deck, several ranks: pose slices of near-equal size
     work = bdist.split_and_partition([(10, 100, 1000)], 4)
     assert sorted(hi - lo for p in work for _, lo, hi in p) == [250, 250, 250, 250]
+
+
+# --- the bench's shard modes -------------------------------------------------
+#
+# bench.py --shard {decks,poses,batch} takes each rank's work from
+# dist.shard_pieces.  Two gloo ranks drive the same function here, with the
+# oracle standing in for the GPU kernel: every pose is evaluated exactly once,
+# the pieces' energies equal the single-process ones, the whole-job rate is
+# total poses over the slowest rank's time, and nothing but the test's own
+# check is exchanged.
+
+def _shard_worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port),
+                      RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    tdist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        out = {}
+        batch = [synth.make_deck([9, i], 2 + i, 20 + 7 * i, 6, 3 + 5 * i) for i in range(6)]
+        shapes = [(len(d["lig_type"]), len(d["pro_type"]), d["poses"].shape[1]) for d in batch]
+        for mode in bdist.SHARD_MODES:
+            pieces, total, scaling = bdist.shard_pieces(mode, rank, world, n_poses=11,
+                                                        batch_shapes=shapes)
+            res = []
+            for d, lo, hi in pieces:
+                if mode == "decks":
+                    D = synth.make_deck(bdist.rank_seed(1, rank), 3, 30, 6, 11)
+                elif mode == "poses":
+                    D = synth.make_deck(1, 3, 30, 6, 11)
+                else:
+                    D = batch[d]
+                res.append((d, lo, hi, oracle.energies(D, D["poses"][:, lo:hi]).tolist()))
+            fake_ms = 4.0 + rank
+            slowest = bdist.max_over_ranks(fake_ms)
+            out[mode] = (res, total, scaling, total / (slowest / 1e3))
+        gathered = [None] * world
+        tdist.all_gather_object(gathered, out)           # test-side check only
+        q.put((rank, gathered))
+    finally:
+        tdist.destroy_process_group()
+
+
+def test_two_gloo_ranks_drive_every_shard_mode():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=180) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    import oracle
+    batch = [synth.make_deck([9, i], 2 + i, 20 + 7 * i, 6, 3 + 5 * i) for i in range(6)]
+    _, gathered = out[0]
+    # decks: each rank all 11 poses of its own deck; weak scaling
+    for r in range(world):
+        res, total, scaling, rate = gathered[r]["decks"]
+        assert scaling == "weak" and total == world * 11
+        (d, lo, hi, E), = res
+        D = synth.make_deck(bdist.rank_seed(1, r), 3, 30, 6, 11)
+        assert (d, lo, hi) == (r, 0, 11)
+        np.testing.assert_array_equal(np.array(E), oracle.energies(D, D["poses"]))
+        assert rate == pytest.approx(total / (4.0 + world - 1) * 1e3)
+    # poses: one deck's poses, each exactly once over the ranks; strong scaling
+    D = synth.make_deck(1, 3, 30, 6, 11)
+    got, seen = np.zeros(11), np.zeros(11, int)
+    for r in range(world):
+        res, total, scaling, _ = gathered[r]["poses"]
+        assert scaling == "strong" and total == 11
+        for d, lo, hi, E in res:
+            got[lo:hi] = E
+            seen[lo:hi] += 1
+    assert np.all(seen == 1)
+    np.testing.assert_array_equal(got, oracle.energies(D, D["poses"]))
+    # batch: every pose of every deck exactly once; strong scaling
+    seen = {i: np.zeros(b["poses"].shape[1], int) for i, b in enumerate(batch)}
+    for r in range(world):
+        res, total, scaling, _ = gathered[r]["batch"]
+        assert scaling == "strong" and total == sum(b["poses"].shape[1] for b in batch)
+        for d, lo, hi, E in res:
+            seen[d][lo:hi] += 1
+            B = batch[d]
+            np.testing.assert_array_equal(np.array(E), oracle.energies(B, B["poses"][:, lo:hi]))
+    assert all(np.all(v == 1) for v in seen.values())
+
+
+def test_shard_pieces_rejects_bad_arguments():
+    with pytest.raises(ValueError):
+        bdist.shard_pieces("rows", 0, 1, n_poses=4)
+    with pytest.raises(ValueError):
+        bdist.shard_pieces("batch", 0, 2)
+    with pytest.raises(ValueError):
+        bdist.shard_pieces("poses", 2, 2, n_poses=4)
+    assert bdist.shard_pieces("poses", 0, 1, n_poses=4) == ([(0, 0, 4)], 4, "strong")
