@@ -180,11 +180,13 @@ BUDE_API int bude_energies_host(bude_deck* deck, const float* poses, int64_t n,
  * decks[i], poses[i] (device [6][n[i]]) and energies[i] (device [n[i]]) for
  * i < count describe independent docking problems of uneven sizes.  All of
  * them run in one launch of a persistent kernel that splits the combined
- * (pose tile x ligand atom x protein atom) space evenly over the grid.  The
- * first call with a given set of arguments builds a plan (work-list
- * descriptors, workspace) and captures the launch into a CUDA graph; calls
- * with the same arguments replay that graph.  Results equal bude_energies'
- * within the variant's rounding (the summation order differs).
+ * (pose tile x ligand atom x protein atom) space over the grid, evenly by
+ * estimated cost (pairs with a desolvation term cost more).  The grid is
+ * capped so that every CTA's share holds at least one unit.  The first call
+ * with a given set of arguments builds a plan (work-list descriptors,
+ * workspace) and captures the launch into a CUDA graph; calls with the same
+ * arguments replay that graph.  Results equal bude_energies' within the
+ * variant's rounding (the summation order differs).
  */
 BUDE_API int bude_energies_batched(bude_deck* const* decks, const float* const* poses,
                           const int64_t* n, float* const* energies,
@@ -396,6 +398,29 @@ BUDE_API const char* bude_last_error(void);
  */
 BUDE_API int bude_debug_fail_alloc(int32_t n);
 BUDE_API int32_t bude_debug_pending_fail_alloc(void);
+
+/*
+ * bude_debug_partition -- test hook: how the persistent kernel would split a
+ * launch over its CTAs, computed on the host by the functions the kernel and
+ * the planner use (no CUDA call; no paper counterpart).
+ *
+ * The launch has count instances; instance i has nt[i] pose tiles of K[i]
+ * units each (K = ligand atoms x protein atoms), each unit costing w[i]
+ * (launches of several instances weight a unit 100 + 40 x its deck's share
+ * of pairs with a desolvation term, and split the total cost evenly).
+ * grid: the CTAs the device could hold.  Outputs: *grid_out, the CTAs the
+ * launch uses; and, each optional (NULL skips it):
+ *   cta_begin[0 .. grid_out]: flat index where each CTA's range starts, the
+ *               last entry one past the end;
+ *   owner[N]:   the CTA whose range holds each flat unit, N = sum nt[i] K[i];
+ *   cover[T]:   how many CTAs the kernel expects to finish each tile,
+ *               T = sum nt[i].
+ * Errors: BUDE_ERR_INVALID_ARG for count < 1, grid < 1, an empty instance or
+ * a NULL size array.
+ */
+BUDE_API int bude_debug_partition(int32_t count, const int64_t* K, const int64_t* nt,
+                                  const int32_t* w, int32_t grid, int32_t* grid_out,
+                                  int64_t* cta_begin, int64_t* owner, int32_t* cover);
 
 #ifdef __cplusplus
 }

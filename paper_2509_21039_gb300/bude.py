@@ -102,6 +102,10 @@ def load(path: str | None = None):
         "bude_last_error": (ctypes.c_char_p, []),
         "bude_debug_fail_alloc": (ci, [i32]),
         "bude_debug_pending_fail_alloc": (i32, []),
+        "bude_debug_partition": (ci, [i32, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                      ctypes.POINTER(i32), i32, ctypes.POINTER(i32),
+                                      ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                      ctypes.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -148,6 +152,26 @@ def debug_fail_alloc(n: int) -> None:
 def debug_pending_fail_alloc() -> int:
     """Allocations left before the injected failure (0 when disarmed)."""
     return int(load().bude_debug_pending_fail_alloc())
+
+
+def debug_partition(K, nt, w, grid: int, with_owner: bool = True):
+    """The kernel's split of a launch over its CTAs (bude_debug_partition):
+    (CTAs used, range starts, owning CTA of every flat unit or None, CTAs
+    expected per tile), all computed on the host."""
+    lib = load()
+    K = np.ascontiguousarray(K, np.int64)
+    nt = np.ascontiguousarray(nt, np.int64)
+    w = np.ascontiguousarray(w, np.int32)
+    g = ctypes.c_int32()
+    begin = np.zeros(int(grid) + 1, np.int64)
+    owner = np.zeros(int((K * nt).sum()), np.int64) if with_owner else None
+    cover = np.zeros(int(nt.sum()), np.int32)
+    P = lambda a, t: a.ctypes.data_as(ctypes.POINTER(t)) if a is not None else None  # noqa: E731
+    _check(lib.bude_debug_partition(len(K), P(K, ctypes.c_int64), P(nt, ctypes.c_int64),
+                                    P(w, ctypes.c_int32), int(grid), ctypes.byref(g),
+                                    P(begin, ctypes.c_int64), P(owner, ctypes.c_int64),
+                                    P(cover, ctypes.c_int32)))
+    return g.value, begin[:g.value + 1].copy(), owner, cover
 
 
 def launch_count() -> int:

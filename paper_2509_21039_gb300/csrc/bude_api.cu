@@ -273,6 +273,25 @@ int chunk_for(const InstanceShape& s, const Resolved& r, bool G, size_t budget)
     return std::max(ch, 1);
 }
 
+// The CTAs a launch over instances inst (their units' costs w, total cost
+// u_total) may use, given at most `grid`.  A launch of several instances
+// splits their cost evenly over the CTAs, and a CTA's range holds at least
+// one unit only if its share of the cost is at least the dearest unit's: a
+// CTA without units inside a tile would be counted among the tile's
+// arrivals and never arrive, leaving the tile unwritten.  So the grid is
+// capped at u_total / (dearest unit).  One instance splits by unit count,
+// and grid <= units suffices.
+long long split_grid(const std::vector<Instance>& inst, long long u_total, long long grid)
+{
+    grid = std::max(1ll, grid);
+    if (inst.size() > 1 && u_total > 0) {
+        long long wmax = 1;
+        for (const Instance& J : inst) wmax = std::max<long long>(wmax, J.w);
+        grid = std::max(1ll, std::min(grid, u_total / wmax));
+    }
+    return grid;
+}
+
 struct Plan {
     std::vector<Instance> inst;
     long long n_total = 0;
@@ -373,7 +392,7 @@ int make_plan(const std::vector<const bude_deck*>& decks, const std::vector<cons
     occ = std::min(occ, r.cps);
     long long grid = (long long)di.sms * occ;
     if (grid > pl->n_total) grid = pl->n_total;
-    pl->grid = (int)std::max(1ll, grid);
+    pl->grid = (int)split_grid(pl->inst, pl->u_total, grid);
     return BUDE_OK;
 }
 
@@ -1241,4 +1260,65 @@ extern "C" BUDE_API int bude_param_grad(bude_deck* deck, const float* poses, int
        "reduction launch");
     g_launches = 3;
     return device_checks(s);
+}
+
+// ---------------------------------------------------------------------------
+// Test hook: the persistent kernel's work split, computed on the host by the
+// functions the kernel and the planner use (no CUDA call).
+// ---------------------------------------------------------------------------
+extern "C" BUDE_API int bude_debug_partition(int32_t count, const int64_t* K, const int64_t* nt,
+                                             const int32_t* w, int32_t grid, int32_t* grid_out,
+                                             int64_t* cta_begin, int64_t* owner, int32_t* cover)
+{
+    if (count < 1 || !K || !nt || !w || grid < 1 || !grid_out)
+        return fail(BUDE_ERR_INVALID_ARG, "bude_debug_partition: bad arguments");
+    std::vector<Instance> inst;
+    long long k = 0, u = 0, tiles = 0;
+    for (int i = 0; i < count; ++i) {
+        if (K[i] < 1 || nt[i] < 1 || w[i] < 1)
+            return fail(BUDE_ERR_INVALID_ARG, "bude_debug_partition: instance %d is empty", i);
+        Instance I;
+        memset(&I, 0, sizeof I);
+        I.k_begin = k;
+        I.k_end = k + nt[i] * K[i];
+        I.tile_begin = tiles;
+        I.w = w[i];
+        I.u_begin = u;
+        u += (I.k_end - I.k_begin) * (long long)I.w;
+        k = I.k_end;
+        tiles += nt[i];
+        inst.push_back(I);
+    }
+    const long long C = split_grid(inst, u, std::min<long long>(grid, k));
+    *grid_out = (int32_t)C;
+    // the launch parameters the kernel would see (launch_plan)
+    Args a;
+    memset(&a, 0, sizeof a);
+    a.n_inst = count;
+    a.single = inst[0];
+    a.table = inst.data();
+    a.n_total = k;
+    a.u_total = count > 1 ? u : 0;
+    const bool weighted = a.u_total > 0 && a.n_inst > 1;
+    const long long N = a.n_total, U = a.u_total;
+    // the same range and owner expressions as pose_kernel
+    if (cta_begin) {
+        for (long long c = 0; c < C; ++c)
+            cta_begin[c] = weighted ? k_of_cost(a, (c * U + C - 1) / C) : c * N / C;
+        cta_begin[C] = weighted ? k_of_cost(a, (C * U + C - 1) / C) : N;
+    }
+    for (size_t i = 0; i < inst.size(); ++i) {
+        const Instance& I = inst[i];
+        auto own = [&](long long kk) {
+            return weighted ? owner_cta_weighted(kk, I, U, C) : owner_cta(kk, N, C);
+        };
+        if (owner)
+            for (long long kk = I.k_begin; kk < I.k_end; ++kk) owner[kk] = own(kk);
+        if (cover)
+            for (long long t = 0; t < nt[i]; ++t) {
+                const long long k0 = I.k_begin + t * K[i];
+                cover[I.tile_begin + t] = (int32_t)(own(k0 + K[i] - 1) - own(k0) + 1);
+            }
+    }
+    return BUDE_OK;
 }

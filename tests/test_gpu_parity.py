@@ -98,6 +98,34 @@ def test_small_config_seed0_every_variant():
         assert err.max() <= GATE[v], (v, err.max())
 
 
+@pytest.mark.parametrize("variant,ppwi,block", [("fast", 16, 384), ("ieee", 8, 256),
+                                                ("comp", 4, 256), ("fast", 2, 128)])
+def test_partial_last_tile_every_size_class(variant, ppwi, block):
+    """Pose counts that are not a multiple of the 32 P-pose tile: the last
+    tile's lanes beyond the count compute a clamped pose and write nothing.
+    Tails of 1, 63, 64, 65 poses, one pose either side of half a tile and one
+    short of a full tile, alone and after two full tiles; energies and pose
+    gradients against the oracle."""
+    TP = 32 * ppwi
+    tails = sorted({1, 63, 64, 65, TP // 2 - 1, TP // 2 + 1, TP - 1} - {0})
+    D = synth.make_deck(109, 12, 300, 34, 2 * TP + TP - 1)
+    deck = bude.Deck(D, device=DEV)
+    for n in [t for t in tails if t < TP] + [2 * TP + t for t in tails if t < TP]:
+        P = np.ascontiguousarray(D["poses"][:, :n])
+        ref, A = oracle.energies(D, P, n_threads=-1, with_abs=True)
+        E = bude.energies(deck, torch.from_numpy(P).to(DEV), variant=variant, ppwi=ppwi,
+                          block=block).cpu().numpy()
+        assert scaled_error(E, ref, A).max() <= GATE[variant], (n, variant, ppwi)
+        if variant != "comp":
+            Eg, G = bude.pose_grad(deck, torch.from_numpy(P).to(DEV), variant=variant,
+                                   ppwi=min(ppwi, 8), block=256)
+            Eref, Gref, S = oracle.pose_grad(D, P, n_threads=-1, with_scale=True)
+            g = G.cpu().numpy().astype(np.float64)
+            err = max(np.max(np.abs(g[:3] - Gref[:3]) / np.maximum(S[0], 1)),
+                      np.max(np.abs(g[3:] - Gref[3:]) / np.maximum(S[1], 1)))
+            assert err <= 1e-4, (n, variant, err)
+
+
 def test_deterministic_repeat():
     D = synth.make_deck(105, 20, 500, 34, 2048)
     deck = bude.Deck(D, device=DEV)
@@ -426,6 +454,32 @@ def test_batched_full_64_deck_workload_sampled_against_oracle(variant):
     assert worst <= GATE[variant], worst
     for d in decks:
         d.close()
+
+
+@pytest.mark.parametrize("shape", [((5, 1, 0), (4, 5, 2)), ((1, 2, 1), (3, 6, 2)),
+                                   ((5, 1, 2), (20, 1, 0)), ((2, 3, 0), (7, 2, 2), (1, 9, 1))])
+@pytest.mark.parametrize("variant,ppwi", [("fast", 16), ("ieee", 1)])
+def test_batched_tiny_launch_every_tile_finished(shape, variant, ppwi):
+    """Batched launches of a few dozen units, where one unit's cost is close
+    to a CTA's share of the total: every CTA's piece must hold at least one
+    unit, or a tile would count an arrival that never comes and stay
+    unwritten (the outputs start as NaN to catch that).  hb pattern 0: no
+    polar type, 1: all polar, 2: half polar, so the units' costs differ."""
+    decks_np = []
+    for i, (nl, npro, pattern) in enumerate(shape):
+        d = synth.make_deck([19, i], nl, npro, 6, 37 + 11 * i)
+        d["hbtype"][:] = {0: 0, 1: 1, 2: np.arange(6) % 2}[pattern]
+        decks_np.append(d)
+    decks = [bude.Deck(d, device=DEV) for d in decks_np]
+    poses = [torch.from_numpy(d["poses"]).to(DEV) for d in decks_np]
+    outs = [torch.full((p.shape[1],), float("nan"), device=DEV) for p in poses]
+    bude.energies_batched(decks, poses, outs, variant=variant, ppwi=ppwi, block=128)
+    torch.cuda.synchronize()
+    for dnp, o in zip(decks_np, outs):
+        ref, A = oracle.energies(dnp, dnp["poses"], n_threads=-1, with_abs=True)
+        E = o.cpu().numpy()
+        assert np.isfinite(E).all()
+        assert scaled_error(E, ref, A).max() <= GATE[variant]
 
 
 def test_batched_with_empty_instances():

@@ -236,3 +236,75 @@ def test_bench_summary_is_compact_and_last(bench):
     assert json.dumps(line["summary"]) in tail
     assert line["summary"]["batched"]["speedup"] == 1.123
     assert line["summary"]["headline"]["eq3_frac"] == 0.8687
+
+
+# --- the persistent kernel's work split (computed on the host by the same
+# functions the kernel uses, through bude_debug_partition) -------------------
+
+def _check_partition(K, nt, w, grid, with_owner=True):
+    g, begin, owner, cover = bude.debug_partition(K, nt, w, grid, with_owner)
+    N = int(sum(int(k) * int(t) for k, t in zip(K, nt)))
+    assert 1 <= g <= grid and g <= N
+    # the CTAs' ranges tile the flat space in order, and none is empty
+    assert begin[0] == 0 and begin[-1] == N
+    assert np.all(np.diff(begin) >= 1)
+    # each tile expects exactly the CTAs whose ranges meet it (ranges are
+    # contiguous and non-empty, so those are the owners of its first and last
+    # unit and every CTA between them)
+    starts = np.cumsum([0] + [int(k) * int(t) for k, t in zip(K, nt)])
+    t_global = 0
+    for (k, t), s0 in zip(zip(K, nt), starts):
+        for j in range(int(t)):
+            k0, k1 = s0 + j * int(k), s0 + (j + 1) * int(k)
+            first = np.searchsorted(begin, k0, side="right") - 1
+            last = np.searchsorted(begin, k1 - 1, side="right") - 1
+            assert cover[t_global] == last - first + 1
+            t_global += 1
+    if owner is not None:
+        # every unit's owner is the CTA whose range holds it
+        np.testing.assert_array_equal(owner, np.repeat(np.arange(g), np.diff(begin)))
+        # partial slots (CTA + tile) of split tiles are unique and in range
+        slots = set()
+        t_global = 0
+        for (k, t), s0 in zip(zip(K, nt), starts):
+            for j in range(int(t)):
+                cov = np.unique(owner[s0 + j * int(k):s0 + (j + 1) * int(k)])
+                if len(cov) > 1:
+                    for c in cov:
+                        sl = int(c) + t_global
+                        assert sl < g + len(cover) and sl not in slots
+                        slots.add(sl)
+                t_global += 1
+    return g
+
+
+def test_work_split_random_launches():
+    rng = np.random.default_rng(21)
+    for trial in range(600):
+        n = int(rng.integers(1, 7))
+        K = rng.integers(1, 60, n)
+        nt = rng.integers(1, 6, n)
+        w = rng.integers(50, 170, n)
+        _check_partition(K, nt, w, int(rng.integers(1, 80)))
+
+
+def test_work_split_where_a_unit_outweighs_a_cta_share():
+    """Few units, one dearer than a CTA's share of the total: the grid shrinks
+    until every CTA's range holds a unit (a CTA without units inside a tile
+    would be counted among the tile's arrivals and never arrive, leaving the
+    tile unwritten)."""
+    for K, nt, w, grid in (([5, 20], [1, 1], [140, 158], 29), ([1, 3], [2, 6], [124, 70], 27),
+                           ([5, 20], [1, 1], [100, 120], 152)):
+        g = _check_partition(K, nt, w, grid)
+        assert g < min(grid, sum(k * t for k, t in zip(K, nt)))
+
+
+def test_work_split_of_the_batched_workload():
+    """The 64-deck batch on one CTA per SM of a GB300: all 152 CTAs, every
+    range non-empty, every tile's expected arrivals equal to the CTAs that
+    meet it."""
+    shapes = synth.batched_shapes(3, 64)
+    K = [nl * npro for nl, npro, _ in shapes]
+    nt = [-(-n // 512) for _, _, n in shapes]
+    w = [100 + (17 * i) % 40 for i in range(64)]
+    assert _check_partition(K, nt, w, 152, with_owner=False) == 152
