@@ -710,8 +710,12 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
+    # collectives run while every rank is in the timed part; once the other
+    # ranks have left, rank 0 times alone
+    together = [world > 1]
+
     def barrier():
-        if world > 1:
+        if together[0]:
             dist.barrier()
 
     shape = dict(SMALL if args.small else FULL)
@@ -859,6 +863,11 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
+    together[0] = False
+    if world > 1:
+        # the single-GPU extras and the host-side oracle belong to the N = 1 line
+        args.no_extras = True
+        args.no_cpu_baseline = True
 
     peaks = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
