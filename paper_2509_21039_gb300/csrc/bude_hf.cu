@@ -37,6 +37,44 @@ namespace bude {
 
 constexpr double kPi = 3.14159265358979323846;
 
+// FP32 integrals take erf(x)/x, x = sqrt(t), from a table instead of erff:
+// with F_k(t) = int_0^1 u^2k exp(-t u^2) du (the Boys functions, F_0(t) =
+// (sqrt(pi)/2) erf(sqrt t)/sqrt t, dF_k/dt = -F_(k+1)), its Taylor expansion
+// about the nearest grid point t_i = i/16,
+//   erf(x)/x = (2/sqrt(pi)) sum_k F_k(t_i) (t_i - t)^k / k!,  k = 0..3,
+// leaves at most (1/32)^4/4! F_4 < 5e-9 for |t - t_i| <= 1/32, 3e-8 of the
+// smallest value on the grid.  Beyond t = 32, erf(sqrt t) is 1 to FP32
+// precision (erfc(sqrt 32) < 2e-15) and erf(x)/x = 1/sqrt(t).  The grid
+// values are computed once per plan on the host in FP64 from the series
+// F_k(t) = exp(-t) sum_j (2t)^j / ((2k+1)(2k+3)...(2k+2j+1)), whose terms are
+// all positive.
+constexpr int kBoysPerUnit = 16;
+constexpr int kBoysTmax = 32;
+constexpr int kBoysN = kBoysTmax * kBoysPerUnit + 1;
+
+void boys_table(std::vector<float4>& tab)
+{
+    tab.resize(kBoysN);
+    const double two_over_sqrt_pi = 2.0 / std::sqrt(kPi);
+    for (int i = 0; i < kBoysN; ++i) {
+        const double t = (double)i / kBoysPerUnit;
+        double F[4];
+        for (int k = 0; k < 4; ++k) {
+            double term = 1.0 / (2 * k + 1), sum = term;
+            for (int j = 1; j < 400; ++j) {
+                term *= 2.0 * t / (2 * k + 2 * j + 1);
+                sum += term;
+                if (term < 1e-18 * sum) break;
+            }
+            F[k] = std::exp(-t) * sum;
+        }
+        // Horner coefficients in d = t - t_i: F0 - d F1 + d^2 F2 / 2 - d^3 F3 / 6
+        tab[(size_t)i] = make_float4((float)(two_over_sqrt_pi * F[0]), (float)(-two_over_sqrt_pi * F[1]),
+                                     (float)(two_over_sqrt_pi * F[2] / 2.0),
+                                     (float)(-two_over_sqrt_pi * F[3] / 6.0));
+    }
+}
+
 struct HfPlanDev {
     int n, ng;
     long long m;          // unique pairs n(n+1)/2
@@ -56,6 +94,7 @@ struct HfPlanDev {
     const float4* rpqf;
     const float* rkpf;
     const int2* rpairs;     // [m] (i, j) of the pair of each rank
+    const float4* boys;     // [kBoysN] FP32 integrals' table of erf(x)/x (below)
 };
 
 __device__ __forceinline__ void pair_of(long long ij, int* i, int* j)
@@ -107,12 +146,21 @@ __device__ __forceinline__ double erf_over_x(double x2)
     const double r = rsqrt(y);
     return erf(y * r) * r;
 }
-__device__ __forceinline__ float erf_over_x(float x2)
+// erf(x)/x from x^2 = t by the table above (tab in shared memory): round 16 t
+// to the nearest grid index with the 1.5 2^23 shift, so that the index is in
+// the low mantissa bits and the grid point is exact, then three FMAs.
+__device__ __forceinline__ float erf_over_x(float t, const float4* __restrict__ tab)
 {
-    const float y = fmaxf(x2, 1e-30f);
-    const float r = rsqrtf(y);
-    return erff(y * r) * r;
+    constexpr float kShift = 12582912.f;   // 1.5 * 2^23: its ulp is 1
+    const float tc = fminf(t, (float)kBoysTmax);
+    const float y = fmaf(tc, (float)kBoysPerUnit, kShift);
+    const int i = __float_as_int(y) - __float_as_int(kShift);
+    const float d = fmaf(y - kShift, -1.f / kBoysPerUnit, tc);
+    const float4 c = tab[i];
+    const float f = fmaf(fmaf(fmaf(c.w, d, c.z), d, c.y), d, c.x);
+    return t < (float)kBoysTmax ? f : rsqrtf(t);
 }
+__device__ __forceinline__ double erf_over_x(double x2, const float4*) { return erf_over_x(x2); }
 
 // Precision-matched helpers for the template below (declared before it, so
 // that the float instantiation never promotes to double).
@@ -150,7 +198,8 @@ __device__ __forceinline__ T contracted(const T4* __restrict__ A, const T4* __re
 // G2 = 0: g2 at run time.
 template <typename T, typename T4, int G2>
 __device__ __forceinline__ T contracted_ranked(const T4* __restrict__ pq, const T* __restrict__ kp,
-                                               long long m, long long a, long long b, int g2)
+                                               long long m, long long a, long long b, int g2,
+                                               const float4* __restrict__ tab)
 {
     if constexpr (G2 > 0) {
         T4 c[G2];
@@ -174,7 +223,7 @@ __device__ __forceinline__ T contracted_ranked(const T4* __restrict__ pq, const 
                 const T dx = x.x - c[cd].x, dy = x.y - c[cd].y, dz = x.z - c[cd].z;
                 const T r2 = hf_fma(dz, dz, hf_fma(dy, dy, dx * dx));
                 const T rs = hf_rsqrt(x.w + c[cd].w);   // sqrt(rho)
-                w = hf_fma(kc[cd] * rs, erf_over_x(r2 * rs * rs), w);
+                w = hf_fma(kc[cd] * rs, erf_over_x(r2 * rs * rs, tab), w);
             }
             v = hf_fma(ka, w, v);
         }
@@ -190,7 +239,7 @@ __device__ __forceinline__ T contracted_ranked(const T4* __restrict__ pq, const 
             const T dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;
             const T r2 = hf_fma(dz, dz, hf_fma(dy, dy, dx * dx));
             const T rs = hf_rsqrt(x.w + c.w);   // sqrt(rho)
-            w = hf_fma(kp[cd * m + b] * rs, erf_over_x(r2 * rs * rs), w);
+            w = hf_fma(kp[cd * m + b] * rs, erf_over_x(r2 * rs * rs, tab), w);
         }
         v = hf_fma(ka, w, v);
     }
@@ -319,6 +368,14 @@ __global__ void __launch_bounds__(128, 1) hf_fock_kernel(const HfPlanDev P,
     const long long per = ((total + warps - 1) / warps + 31) & ~31ll;
     const long long x0 = warp * per, x1 = min(total, x0 + per);
     const int g2 = P.ng * P.ng;
+    // FP32 integrals: the erf(x)/x table, staged once per CTA
+    const float4* tab = nullptr;
+    if constexpr (F32) {
+        __shared__ float4 s_boys[kBoysN];
+        for (int e = threadIdx.x; e < kBoysN; e += blockDim.x) s_boys[e] = P.boys[e];
+        __syncthreads();
+        tab = s_boys;
+    }
     long long a = -1;
     for (long long x = x0 + lane; x < x1; x += 32) {
         if (a < 0) {
@@ -334,8 +391,8 @@ __global__ void __launch_bounds__(128, 1) hf_fock_kernel(const HfPlanDev P,
         const long long b = x - prefix[a];
         const int2 pij = P.rpairs[a], pkl = P.rpairs[b];
         const int i = pij.x, j = pij.y, k = pkl.x, l = pkl.y;
-        double v = F32 ? (double)contracted_ranked<float, float4, G2>(P.rpqf, P.rkpf, P.m, a, b, g2)
-                       : contracted_ranked<double, double4_32a, G2>(P.rpq, P.rkp, P.m, a, b, g2);
+        double v = F32 ? (double)contracted_ranked<float, float4, G2>(P.rpqf, P.rkpf, P.m, a, b, g2, tab)
+                       : contracted_ranked<double, double4_32a, G2>(P.rpq, P.rkp, P.m, a, b, g2, tab);
         if (i == j) v *= 0.5;
         if (k == l) v *= 0.5;
         if (a == b) v *= 0.5;
@@ -426,6 +483,7 @@ struct bude_hf {
     float4* rpqf = nullptr;
     float* rkpf = nullptr;
     int2* rpairs = nullptr;      // [m]
+    float4* boys = nullptr;      // [kBoysN]
     HfPlanDev view() const
     {
         HfPlanDev v;
@@ -445,6 +503,7 @@ struct bude_hf {
         v.rpqf = rpqf;
         v.rkpf = rkpf;
         v.rpairs = rpairs;
+        v.boys = boys;
         return v;
     }
 };
@@ -472,6 +531,7 @@ extern "C" BUDE_API int bude_hf_destroy(bude_hf* h)
     cudaFree(h->rpqf);
     cudaFree(h->rkpf);
     cudaFree(h->rpairs);
+    cudaFree(h->boys);
     delete h;
     return BUDE_OK;
 }
@@ -515,10 +575,14 @@ extern "C" BUDE_API int bude_hf_create(int32_t n_atoms, const double* geom, int3
         dev_alloc((void**)&h->rkp, e * sizeof(double)) ||
         dev_alloc((void**)&h->rpqf, e * sizeof(float4)) ||
         dev_alloc((void**)&h->rkpf, e * sizeof(float)) ||
-        dev_alloc((void**)&h->rpairs, (size_t)h->m * sizeof(int2)))
+        dev_alloc((void**)&h->rpairs, (size_t)h->m * sizeof(int2)) ||
+        dev_alloc((void**)&h->boys, kBoysN * sizeof(float4)))
         return bail(BUDE_ERR_OOM);
     // host inputs: copied synchronously (plan creation is not on the hot path)
-    if (cudaMemcpy(h->geom, geom, 3 * sizeof(double) * n_atoms, cudaMemcpyHostToDevice) ||
+    std::vector<float4> boys;
+    boys_table(boys);
+    if (cudaMemcpy(h->boys, boys.data(), kBoysN * sizeof(float4), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(h->geom, geom, 3 * sizeof(double) * n_atoms, cudaMemcpyHostToDevice) ||
         cudaMemcpy(h->xc, xpnt, sizeof(double) * ngauss, cudaMemcpyHostToDevice) ||
         cudaMemcpy(h->xc + ngauss, coef, sizeof(double) * ngauss, cudaMemcpyHostToDevice))
         return bail(BUDE_ERR_CUDA);
