@@ -51,27 +51,49 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kBoysPerUnit = 16;
 constexpr int kBoysTmax = 32;
 constexpr int kBoysN = kBoysTmax * kBoysPerUnit + 1;
+// The FP64 kernel's table: t_i = i/32 up to t = 36 (erfc(6) < 2.2e-17, so
+// erf(x)/x = 1/sqrt(t) in FP64 beyond it) and six Taylor terms: at most
+// (1/64)^6/6! F_6 < 1.6e-15, 9e-15 of the smallest value on the grid.
+constexpr int kBoys64PerUnit = 32;
+constexpr int kBoys64Tmax = 36;
+constexpr int kBoys64N = kBoys64Tmax * kBoys64PerUnit + 1;
+constexpr int kBoys64Terms = 6;
+
+// (2/sqrt(pi)) (-1)^k F_k(t) / k!, k < terms: the Horner coefficients of
+// erf(x)/x in d = t' - t about t.
+void boys_coefficients(double t, int terms, double* c)
+{
+    const double two_over_sqrt_pi = 2.0 / std::sqrt(kPi);
+    double fact = 1.0;
+    for (int k = 0; k < terms; ++k) {
+        double term = 1.0 / (2 * k + 1), sum = term;
+        for (int j = 1; j < 600; ++j) {
+            term *= 2.0 * t / (2 * k + 2 * j + 1);
+            sum += term;
+            if (term < 1e-18 * sum) break;
+        }
+        if (k > 0) fact *= k;
+        c[k] = ((k & 1) ? -1.0 : 1.0) * two_over_sqrt_pi * std::exp(-t) * sum / fact;
+    }
+}
 
 void boys_table(std::vector<float4>& tab)
 {
     tab.resize(kBoysN);
-    const double two_over_sqrt_pi = 2.0 / std::sqrt(kPi);
     for (int i = 0; i < kBoysN; ++i) {
-        const double t = (double)i / kBoysPerUnit;
-        double F[4];
-        for (int k = 0; k < 4; ++k) {
-            double term = 1.0 / (2 * k + 1), sum = term;
-            for (int j = 1; j < 400; ++j) {
-                term *= 2.0 * t / (2 * k + 2 * j + 1);
-                sum += term;
-                if (term < 1e-18 * sum) break;
-            }
-            F[k] = std::exp(-t) * sum;
-        }
-        // Horner coefficients in d = t - t_i: F0 - d F1 + d^2 F2 / 2 - d^3 F3 / 6
-        tab[(size_t)i] = make_float4((float)(two_over_sqrt_pi * F[0]), (float)(-two_over_sqrt_pi * F[1]),
-                                     (float)(two_over_sqrt_pi * F[2] / 2.0),
-                                     (float)(-two_over_sqrt_pi * F[3] / 6.0));
+        double c[4];
+        boys_coefficients((double)i / kBoysPerUnit, 4, c);
+        tab[(size_t)i] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)c[3]);
+    }
+}
+
+void boys_table64(std::vector<double2>& tab)
+{
+    tab.resize((size_t)kBoys64N * 3);
+    for (int i = 0; i < kBoys64N; ++i) {
+        double c[kBoys64Terms];
+        boys_coefficients((double)i / kBoys64PerUnit, kBoys64Terms, c);
+        for (int h = 0; h < 3; ++h) tab[(size_t)i * 3 + h] = make_double2(c[2 * h], c[2 * h + 1]);
     }
 }
 
@@ -95,6 +117,7 @@ struct HfPlanDev {
     const float* rkpf;
     const int2* rpairs;     // [m] (i, j) of the pair of each rank
     const float4* boys;     // [kBoysN] FP32 integrals' table of erf(x)/x (below)
+    const double2* boys64;  // [kBoys64N][3] the FP64 kernel's
 };
 
 __device__ __forceinline__ void pair_of(long long ij, int* i, int* j)
@@ -160,7 +183,23 @@ __device__ __forceinline__ float erf_over_x(float t, const float4* __restrict__ 
     const float f = fmaf(fmaf(fmaf(c.w, d, c.z), d, c.y), d, c.x);
     return t < (float)kBoysTmax ? f : rsqrtf(t);
 }
-__device__ __forceinline__ double erf_over_x(double x2, const float4*) { return erf_over_x(x2); }
+// The same in FP64 with the finer table (read through the L1 cache: 55 KB),
+// the 1.5 2^52 shift and five FMAs.
+__device__ __forceinline__ double erf_over_x(double t, const double2* __restrict__ tab)
+{
+    constexpr double kShift = 6755399441055744.0;   // 1.5 * 2^52: its ulp is 1
+    const double tc = fmin(t, (double)kBoys64Tmax);
+    const double y = fma(tc, (double)kBoys64PerUnit, kShift);
+    const long long i = __double_as_longlong(y) - __double_as_longlong(kShift);
+    const double d = fma(y - kShift, -1.0 / kBoys64PerUnit, tc);
+    const double2 c01 = __ldg(tab + 3 * i), c23 = __ldg(tab + 3 * i + 1), c45 = __ldg(tab + 3 * i + 2);
+    double f = fma(c45.y, d, c45.x);
+    f = fma(f, d, c23.y);
+    f = fma(f, d, c23.x);
+    f = fma(f, d, c01.y);
+    f = fma(f, d, c01.x);
+    return t < (double)kBoys64Tmax ? f : rsqrt(t);
+}
 
 // Precision-matched helpers for the template below (declared before it, so
 // that the float instantiation never promotes to double).
@@ -196,10 +235,10 @@ __device__ __forceinline__ T contracted(const T4* __restrict__ A, const T4* __re
 // with the partner's G2 products loaded up front (all in flight at once) and
 // kept in registers across the loop over ab, whose body is unrolled over cd;
 // G2 = 0: g2 at run time.
-template <typename T, typename T4, int G2>
+template <typename T, typename T4, int G2, typename TAB>
 __device__ __forceinline__ T contracted_ranked(const T4* __restrict__ pq, const T* __restrict__ kp,
                                                long long m, long long a, long long b, int g2,
-                                               const float4* __restrict__ tab)
+                                               const TAB* __restrict__ tab)
 {
     if constexpr (G2 > 0) {
         T4 c[G2];
@@ -392,7 +431,8 @@ __global__ void __launch_bounds__(128, 1) hf_fock_kernel(const HfPlanDev P,
         const int2 pij = P.rpairs[a], pkl = P.rpairs[b];
         const int i = pij.x, j = pij.y, k = pkl.x, l = pkl.y;
         double v = F32 ? (double)contracted_ranked<float, float4, G2>(P.rpqf, P.rkpf, P.m, a, b, g2, tab)
-                       : contracted_ranked<double, double4_32a, G2>(P.rpq, P.rkp, P.m, a, b, g2, tab);
+                       : contracted_ranked<double, double4_32a, G2>(P.rpq, P.rkp, P.m, a, b, g2,
+                                                                    P.boys64);
         if (i == j) v *= 0.5;
         if (k == l) v *= 0.5;
         if (a == b) v *= 0.5;
@@ -484,6 +524,7 @@ struct bude_hf {
     float* rkpf = nullptr;
     int2* rpairs = nullptr;      // [m]
     float4* boys = nullptr;      // [kBoysN]
+    double2* boys64 = nullptr;   // [kBoys64N][3]
     HfPlanDev view() const
     {
         HfPlanDev v;
@@ -504,6 +545,7 @@ struct bude_hf {
         v.rkpf = rkpf;
         v.rpairs = rpairs;
         v.boys = boys;
+        v.boys64 = boys64;
         return v;
     }
 };
@@ -532,6 +574,7 @@ extern "C" BUDE_API int bude_hf_destroy(bude_hf* h)
     cudaFree(h->rkpf);
     cudaFree(h->rpairs);
     cudaFree(h->boys);
+    cudaFree(h->boys64);
     delete h;
     return BUDE_OK;
 }
@@ -576,12 +619,16 @@ extern "C" BUDE_API int bude_hf_create(int32_t n_atoms, const double* geom, int3
         dev_alloc((void**)&h->rpqf, e * sizeof(float4)) ||
         dev_alloc((void**)&h->rkpf, e * sizeof(float)) ||
         dev_alloc((void**)&h->rpairs, (size_t)h->m * sizeof(int2)) ||
-        dev_alloc((void**)&h->boys, kBoysN * sizeof(float4)))
+        dev_alloc((void**)&h->boys, kBoysN * sizeof(float4)) ||
+        dev_alloc((void**)&h->boys64, (size_t)kBoys64N * 3 * sizeof(double2)))
         return bail(BUDE_ERR_OOM);
     // host inputs: copied synchronously (plan creation is not on the hot path)
     std::vector<float4> boys;
     boys_table(boys);
+    std::vector<double2> boys64;
+    boys_table64(boys64);
     if (cudaMemcpy(h->boys, boys.data(), kBoysN * sizeof(float4), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(h->boys64, boys64.data(), boys64.size() * sizeof(double2), cudaMemcpyHostToDevice) ||
         cudaMemcpy(h->geom, geom, 3 * sizeof(double) * n_atoms, cudaMemcpyHostToDevice) ||
         cudaMemcpy(h->xc, xpnt, sizeof(double) * ngauss, cudaMemcpyHostToDevice) ||
         cudaMemcpy(h->xc + ngauss, coef, sizeof(double) * ngauss, cudaMemcpyHostToDevice))

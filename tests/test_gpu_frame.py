@@ -77,6 +77,17 @@ def test_other_variants_far_from_origin(deck0, variant, ppwi):
     assert err <= GATE[variant], (variant, ppwi, err)
 
 
+@pytest.mark.parametrize("variant,ppwi,block", [("fast", 16, 384), ("ieee", 16, 384),
+                                                ("comp", 8, 256)])
+def test_ten_thousand_angstrom_from_origin(deck0, variant, ppwi, block):
+    """At 1e4 A a float32 coordinate resolves only 1e-3 A, and the oracle
+    scores the inputs as given.  The deck's frame shift and the translations'
+    shift are differences of floats within a factor of two of each other,
+    hence exact, so the kernels still see the small coordinates."""
+    err = energies_err(shifted(deck0, 1.0e4), variant, ppwi=ppwi, block=block)
+    assert err <= GATE[variant], (variant, err)
+
+
 def test_fp64_far_from_origin(deck0):
     """The FP64 kernel reads the atoms as given: still within 1e-12 plus the
     float32 rounding of the output."""
