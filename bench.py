@@ -41,27 +41,27 @@ FP32_LANES_PER_SM = 128
 # kernel and shape (dram__bytes_read.sum + dram__bytes_write.sum, mean of 9
 # launches).  Reported only while the kernel source and the launch shape are
 # the ones that were measured; otherwise the line says why it is missing.
-MEASURED_TRAFFIC = {"kernel_sha256_16": "955ceb2c81207afb", "variant": "fast", "ppwi": 16,
-                    "block": 384, "bytes": 1890759.0}
+MEASURED_TRAFFIC = {"kernel_sha256_16": "52e75f3fab9b3ede", "variant": "fast", "ppwi": 16,
+                    "block": 384, "bytes": 1871161.0}
 
 # FP32 FLOPs the kernel executes per pose-pair on the full deck, from ncu's
 # per-opcode thread-instruction counters of the same launch (FADD, FMUL 1;
 # FFMA, FADD2, FMUL2 2; FFMA2 4), per variant, for the kernel source with
 # this hash.  Fewer than Eq. 3's 30: zero desolvation runs are skipped, and
 # FAST takes the steric term as sign(H) z^2 with one fewer operation.
-MEASURED_EXECUTED = {"kernel_sha256_16": "955ceb2c81207afb",
+MEASURED_EXECUTED = {"kernel_sha256_16": "52e75f3fab9b3ede",
                      "flop_per_pair": {"fast": 22.24, "ieee": 29.25, "comp": 29.24}}
 
 # The same count for the FAST adjoint (energies and pose gradients) at P = 8
 # on the 64 x 2672 x 16384 workload: the force and torque sums add the
 # reciprocal root's products and three FFMA2 per pose pair to the energy work.
-MEASURED_EXECUTED_ADJOINT = {"kernel_sha256_16": "955ceb2c81207afb", "variant": "fast", "ppwi": 8,
+MEASURED_EXECUTED_ADJOINT = {"kernel_sha256_16": "52e75f3fab9b3ede", "variant": "fast", "ppwi": 8,
                              "flop_per_pair": 36.77}
 
 # The same count for the FAST forcefield-gradient kernel (param_kernel) at
 # P = 8 on the 64 x 2672 x 16384 workload; the hash covers both of its
 # source files.
-MEASURED_EXECUTED_PARAM = {"kernel_sha256_16": "a5a28efa6c9c9d01", "variant": "fast", "ppwi": 8,
+MEASURED_EXECUTED_PARAM = {"kernel_sha256_16": "70c6640ed89d87c5", "variant": "fast", "ppwi": 8,
                            "flop_per_pair": 39.12}
 
 
@@ -690,7 +690,9 @@ def main():
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the pose-gradient (adjoint) extra (profiling)")
     ap.add_argument("--hf-only", type=int, default=0, metavar="ATOMS",
-                    help="only the FP32-integral Fock build on this many atoms (profiling)")
+                    help="only the Fock build on this many atoms (profiling)")
+    ap.add_argument("--hf-variant", default="ieee", choices=["ieee", "fp64"],
+                    help="with --hf-only: FP32 integrals (ieee) or all FP64")
     ap.add_argument("--shard", default="decks", choices=["decks", "poses", "batch"],
                     help="decks: one deck per rank (weak scaling, the default); poses: one "
                          "full-size deck's poses split over the ranks; batch: the 64-deck "
@@ -812,7 +814,8 @@ def main():
         return
 
     if args.hf_only:
-        res = hartree_fock(bude, synth, dev, timed, sizes=(args.hf_only,), variants=("ieee",))
+        res = hartree_fock(bude, synth, dev, timed, sizes=(args.hf_only,),
+                           variants=(args.hf_variant,))
         if rank == 0:
             print(json.dumps({"hartree_fock": res}), flush=True)
         return
