@@ -551,6 +551,38 @@ def hartree_fock(bude, synth, dev, timed, sizes=(64, 128, 256), variants=("ieee"
     return out
 
 
+def arm_config(shard, shape, world, variant, ppwi, block, ctas_per_sm, flush_mb):
+    """config of the JSON line: the workload and the GPU launch it is timed
+    in.  The reference arm reports the same dict for the same run."""
+    return {"workload": workload_name(shard, shape, world),
+            "variant": variant, "ppwi": ppwi, "block": block, "ctas_per_sm": ctas_per_sm,
+            "l2": f"flushed ({flush_mb} MiB write) before every timed step",
+            "parallelism": {"decks": f"independent decks per GPU x{world}",
+                            "poses": f"one deck's poses split over {world} GPUs",
+                            "batch": f"64-deck batch split over {world} GPUs"}[shard],
+            "shard": shard}
+
+
+def default_launch(variant):
+    """(ppwi, block, ctas_per_sm) the GPU arm takes for the full deck: the
+    tuned entry for this GPU (any GB300 entry when no GPU is visible), else
+    the library's compiled-in default shape."""
+    from paper_2509_21039_gb300 import tune
+    table = tune.load_table()
+    suffix = f"|{variant}|plain|{tune.bucket(FULL['n_lig'], FULL['n_pro'], FULL['n_poses'])}"
+    keys = [k for k in table if k.endswith(suffix)]
+    try:
+        import torch
+        if torch.cuda.is_available():
+            keys = [k for k in keys if k.startswith(tune.gpu_name() + "|")] or keys
+    except Exception:
+        pass
+    if keys:
+        e = table[sorted(keys)[0]]
+        return e["ppwi"], e["block"], e["ctas_per_sm"]
+    return 8, 256, 1
+
+
 def workload_name(shard, shape, world):
     """config.workload for a shard mode."""
     deck = (f"{shape['n_lig']} lig x {shape['n_pro']} pro x {shape['n_poses']} poses, "
@@ -655,8 +687,10 @@ def reference_arm(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "full-size FP32 deck 64 lig x 2672 pro x 65536 poses, seed 1",
-                       "l2": "not applicable (host CPU)"},
+            # the GPU arm's config for the same run; the oracle itself runs on the
+            # host (FP64, no L2 flush): its sample is described in cpu_baseline
+            "config": arm_config(args.shard, dict(FULL), args.gpus, args.variant,
+                                 *default_launch(args.variant), args.flush_mb),
             "cpu_baseline": {"value": val, "unit": "poses/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "poses/s", "h2d_bytes_per_step": 0,
@@ -924,14 +958,9 @@ def main():
         "ms_per_step_median": statistics.median(ms), "ms_per_step_best": min(ms),
         "higher_is_better": True, "scaling": scaling, "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(shard, shape, world),
-                   "variant": args.variant, "ppwi": ppwi, "block": block,
-                   "ctas_per_sm": (bopts if shard == "batch" else resolved).ctas_per_sm,
-                   "l2": f"flushed ({args.flush_mb} MiB write) before every timed step",
-                   "parallelism": {"decks": f"independent decks per GPU x{world}",
-                                   "poses": f"one deck's poses split over {world} GPUs",
-                                   "batch": f"64-deck batch split over {world} GPUs"}[shard],
-                   "shard": shard},
+        "config": arm_config(shard, shape, world, args.variant, ppwi, block,
+                             (bopts if shard == "batch" else resolved).ctas_per_sm,
+                             args.flush_mb),
         "gpu_launches": int(launches),
         "e2e": {"value": total_units / (e2e_mean / 1e3), "unit": "poses/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
