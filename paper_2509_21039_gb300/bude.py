@@ -234,12 +234,21 @@ def pack_forcefield(radius, hardness, elsc, hbtype) -> np.ndarray:
     return out
 
 
+def _cuda_device(device=None) -> torch.device:
+    """A CUDA device with its index ("cuda" and None: the current device), so
+    that it compares equal to the device of the tensors made on it."""
+    dev = torch.device(device) if device is not None else torch.device("cuda")
+    if dev.type != "cuda":
+        raise ValueError(f"a CUDA device, got {dev}")
+    return dev if dev.index is not None else torch.device("cuda", torch.cuda.current_device())
+
+
 class Deck:
     """A deck on the current CUDA device (owns the library's deck handle)."""
 
     def __init__(self, deck: dict, device=None, stream=None):
         lib = load()
-        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        dev = _cuda_device(device)
         lig = torch.from_numpy(pack_atoms(deck["lig_xyz"], deck["lig_type"])).to(dev)
         pro = torch.from_numpy(pack_atoms(deck["pro_xyz"], deck["pro_type"])).to(dev)
         ff = torch.from_numpy(pack_forcefield(deck["radius"], deck["hardness"], deck["elsc"],
@@ -450,16 +459,36 @@ def _dtype_code(t: torch.Tensor) -> int:
     raise TypeError("float32 or float64 tensors only")
 
 
+def _check_cuda(ts, what: str):
+    """The kernels read and write these tensors through raw pointers: every
+    one must be a CUDA tensor, all on one device."""
+    for t in ts:
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+            raise ValueError(f"{what} must be CUDA tensors")
+        if t.device != ts[0].device:
+            raise ValueError(f"{what} on {t.device} and {ts[0].device}")
+
+
 def stream_op(op: str, a=None, b=None, c=None, scalar: float = 0.4, dot_out=None, stream=None):
     """One BabelStream operation (copy c=a, mul b=s c, add c=a+b, triad
     a=b+s c, dot) on equal-length contiguous device tensors."""
-    ts = [t for t in (a, b, c) if t is not None]
-    if not ts or any((not t.is_contiguous()) or t.dtype != ts[0].dtype or t.numel() != ts[0].numel()
-                     for t in ts):
-        raise ValueError("contiguous tensors of one dtype and length")
     code = STREAM_OPS[op]
-    if code == 4 and dot_out is None:
-        dot_out = torch.empty((), dtype=torch.float64, device=ts[0].device)
+    given = {"a": a, "b": b, "c": c}
+    need = {0: "ac", 1: "bc", 2: "abc", 3: "abc", 4: "ab"}[code]
+    if any(given[k] is None for k in need):
+        raise ValueError(f"{op} needs the arrays {', '.join(need)}")
+    ts = [given[k] for k in need]
+    _check_cuda(ts, "the arrays")
+    if any((not t.is_contiguous()) or t.dtype != ts[0].dtype or t.numel() != ts[0].numel()
+           for t in ts):
+        raise ValueError("contiguous tensors of one dtype and length")
+    a, b, c = (given[k] if k in need else None for k in "abc")
+    if code == 4:
+        if dot_out is None:
+            dot_out = torch.empty((), dtype=torch.float64, device=ts[0].device)
+        elif not isinstance(dot_out, torch.Tensor) or dot_out.dtype != torch.float64 \
+                or dot_out.numel() != 1 or dot_out.device != ts[0].device:
+            raise ValueError("dot_out must be a one-element float64 tensor on the arrays' device")
     ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
     rc = load().bude_stream(code, _dtype_code(ts[0]), ptr(a), ptr(b), ptr(c), float(scalar),
                             ts[0].numel(), ptr(dot_out), _stream_ptr(stream))
@@ -474,6 +503,7 @@ def laplacian(u: torch.Tensor, f: torch.Tensor, invhx2=1.0, invhy2=1.0, invhz2=1
         raise ValueError("u and f: same [nx, ny, nz] shape and dtype")
     if not (u.is_contiguous() and f.is_contiguous()):
         raise ValueError("contiguous tensors")
+    _check_cuda([u, f], "u and f")
     nx, ny, nz = u.shape
     rc = load().bude_laplacian(_dtype_code(u), ctypes.c_void_p(u.data_ptr()),
                                ctypes.c_void_p(f.data_ptr()), nx, ny, nz, float(invhx2),
@@ -515,8 +545,7 @@ class HartreeFock:
         x = np.ascontiguousarray(xpnt, np.float64)
         c = np.ascontiguousarray(coef, np.float64)
         self.n = g.shape[0]
-        self.device = torch.device(device) if device is not None else torch.device(
-            "cuda", torch.cuda.current_device())
+        self.device = _cuda_device(device)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             rc = lib.bude_hf_create(self.n, g.ctypes.data_as(ctypes.c_void_p), len(x),
@@ -527,8 +556,14 @@ class HartreeFock:
         self._h = h
 
     def fock(self, dens: torch.Tensor, tol: float = 1e-12, variant="fp64", out=None, stream=None):
-        if dens.shape != (self.n, self.n) or dens.dtype != torch.float64 or not dens.is_contiguous():
-            raise ValueError("dens must be a contiguous float64 [n, n] tensor")
+        for t, what in ((dens, "dens"), (out, "out")):
+            if t is None:
+                continue
+            if not isinstance(t, torch.Tensor) or t.shape != (self.n, self.n) \
+                    or t.dtype != torch.float64 or not t.is_contiguous():
+                raise ValueError(f"{what} must be a contiguous float64 [n, n] tensor")
+            if t.device != self.device:
+                raise ValueError(f"{what} on {t.device}, the basis on {self.device}")
         out = torch.empty_like(dens) if out is None else out
         v = VARIANTS[variant] if isinstance(variant, str) else variant
         rc = load().bude_hf_fock(self._h, ctypes.c_void_p(dens.data_ptr()),

@@ -611,3 +611,15 @@ def test_gradient_with_energy_shaped_defaults(variant):
     finally:
         bude.set_default_options(saved)
         deck.close()
+
+
+def test_device_named_without_index_is_the_current_device():
+    # "cuda" and no device at all both mean the current device, and tensors
+    # made there are accepted
+    D = synth.make_deck(5, 6, 40, 34, 33)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    ref = bude.energies(bude.Deck(D, device=DEV), P)
+    for dev in ("cuda", None):
+        deck = bude.Deck(D, device=dev)
+        assert deck.device == torch.device(DEV)
+        assert torch.equal(bude.energies(deck, P), ref)

@@ -112,6 +112,13 @@ def test_calibration_edge_cases():
         bude.stream_op("copy", a=x[1:5], c=x[:4])        # misaligned start
     u = torch.zeros((2, 5, 5), device=DEV)
     bude.laplacian(u, torch.zeros_like(u))              # no interior: no-op
+    # the dot's output: one float64 on the arrays' device, else refused
+    for bad in (torch.empty((), device=DEV), torch.empty(2, dtype=torch.float64, device=DEV),
+                torch.empty((), dtype=torch.float64)):
+        with pytest.raises(ValueError, match="dot_out"):
+            bude.stream_op("dot", a=x, b=x, dot_out=bad)
+    d = torch.full((1,), 7.0, dtype=torch.float64, device=DEV)
+    assert bude.stream_op("dot", a=x + 1, b=x + 2, dot_out=d) is d and d.item() == 16.0
 
 
 def _misaligned_copy(u):

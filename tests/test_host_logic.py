@@ -214,6 +214,33 @@ def test_batched_outputs_are_checked_per_deck():
         bude.energies_batched(decks, poses, outs=[_meta(8), _meta(5, dtype=torch.float16)])
 
 
+def test_stream_stencil_and_fock_refuse_bad_tensors_before_any_launch():
+    # host tensors reach a kernel as host pointers; missing arrays as nulls
+    import torch
+    x = torch.zeros(64)
+    with pytest.raises(ValueError, match="CUDA"):
+        bude.stream_op("copy", a=x, c=x.clone())
+    with pytest.raises(ValueError, match="needs the arrays a, b"):
+        bude.stream_op("dot", a=x)
+    with pytest.raises(ValueError, match="needs the arrays b, c"):
+        bude.stream_op("mul", c=x)
+    with pytest.raises(ValueError, match="CUDA"):
+        bude.laplacian(torch.zeros(4, 4, 4), torch.zeros(4, 4, 4))
+    hf = bude.HartreeFock.__new__(bude.HartreeFock)
+    hf.n, hf.device, hf._h = 4, torch.device("cuda", 0), None
+    with pytest.raises(ValueError, match="dens on cpu"):
+        hf.fock(torch.zeros(4, 4, dtype=torch.float64))
+    hf.device = torch.device("meta")
+    with pytest.raises(ValueError, match="dens must be"):
+        hf.fock(torch.zeros(4, 5, dtype=torch.float64, device="meta"))
+    with pytest.raises(ValueError, match="out must be"):
+        hf.fock(torch.zeros(4, 4, dtype=torch.float64, device="meta"),
+                out=torch.zeros(4, 4, device="meta"))
+    with pytest.raises(ValueError, match="a CUDA device"):
+        bude._cuda_device("cpu")
+    assert bude._cuda_device("cuda:1") == torch.device("cuda", 1)
+
+
 def test_bench_summary_is_compact_and_last(bench):
     """The bench line ends with a rounded summary short enough that a reader
     keeping only the last 1500 characters of the line still sees all of it."""
