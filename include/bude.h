@@ -185,7 +185,9 @@ BUDE_API int bude_energies_host(bude_deck* deck, const float* poses, int64_t n,
  * capped so that every CTA's share holds at least one unit.  The first call
  * with a given set of arguments builds a plan (work-list descriptors,
  * workspace) and captures the launch into a CUDA graph; calls with the same
- * arguments replay that graph.  Results equal bude_energies' within the
+ * arguments replay that graph.  The library keeps the 64 most recently used
+ * plans; a plan dropped to make room is rebuilt by its next call, and its
+ * destruction waits for the device.  Results equal bude_energies' within the
  * variant's rounding (the summation order differs).
  */
 BUDE_API int bude_energies_batched(bude_deck* const* decks, const float* const* poses,
@@ -262,10 +264,12 @@ BUDE_API int bude_selfcheck_sqrt(uint64_t* mismatches, uint32_t* first_bad, void
  * updated in place; energies (device float32 [n]) receives the final E.
  * step0 is in pose units (radians and Angstrom share one step length).
  * The first call with a given argument set allocates the plan's buffers
- * (22 floats per pose) and captures the whole loop -- 2 + 3 x steps kernel
- * launches -- into one CUDA graph; later calls replay it.  Uses the deck's
- * workspace: calls on one deck must not overlap.  Variants and options as
- * bude_pose_grad.
+ * (22 floats per pose, and its own partial-sum workspace, so that later calls
+ * on the deck that resize the deck's workspace leave the graph valid) and
+ * captures the whole loop -- 2 + 3 x steps kernel launches -- into one CUDA
+ * graph; later calls replay it.  The 64 most recently used plans are kept, as
+ * for bude_energies_batched.  Calls with one argument set must not overlap.
+ * Variants and options as bude_pose_grad.
  */
 BUDE_API int bude_refine(bude_deck* deck, float* poses, int64_t n, int32_t steps, float step0,
                          float* energies, const bude_options* opts, void* stream);
@@ -421,6 +425,15 @@ BUDE_API int32_t bude_debug_pending_fail_alloc(void);
 BUDE_API int bude_debug_partition(int32_t count, const int64_t* K, const int64_t* nt,
                                   const int32_t* w, int32_t grid, int32_t* grid_out,
                                   int64_t* cta_begin, int64_t* owner, int32_t* cover);
+
+/*
+ * bude_debug_cached_plans -- test hook: how many captured plans the library
+ * holds for bude_energies_batched (*batched) and bude_refine (*refine); each
+ * cache keeps at most 64 and drops the least recently used one when a call
+ * with a new argument set needs room.  Either pointer may be NULL.  No CUDA
+ * call.
+ */
+BUDE_API int bude_debug_cached_plans(int32_t* batched, int32_t* refine);
 
 #ifdef __cplusplus
 }

@@ -106,6 +106,7 @@ def load(path: str | None = None):
                                       ctypes.POINTER(i32), i32, ctypes.POINTER(i32),
                                       ctypes.POINTER(i64), ctypes.POINTER(i64),
                                       ctypes.POINTER(i32)]),
+        "bude_debug_cached_plans": (ci, [ctypes.POINTER(i32), ctypes.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -172,6 +173,13 @@ def debug_partition(K, nt, w, grid: int, with_owner: bool = True):
                                     P(begin, ctypes.c_int64), P(owner, ctypes.c_int64),
                                     P(cover, ctypes.c_int32)))
     return g.value, begin[:g.value + 1].copy(), owner, cover
+
+
+def debug_cached_plans() -> tuple[int, int]:
+    """(batched, refine): captured plans the library holds (at most 64 each)."""
+    b, r = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().bude_debug_cached_plans(ctypes.byref(b), ctypes.byref(r)))
+    return b.value, r.value
 
 
 def launch_count() -> int:

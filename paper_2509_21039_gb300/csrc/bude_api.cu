@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -544,6 +545,76 @@ int run_single(bude_deck* deck, const float* poses, int64_t n, float* energies, 
     return device_checks(s);
 }
 
+// ---- caches of captured plans ----------------------------------------------
+//
+// Batched and refinement calls capture a CUDA graph per argument set and
+// replay it.  A cache keeps at most kMaxCachedPlans of them and drops the
+// least recently used when a new one comes in.  Callers hold a shared_ptr
+// while they enqueue a replay, so a plan that another thread drops is
+// destroyed only after that; a plan's destructor waits for the device before
+// it frees the buffers a replay still in flight may use.  The caches are
+// never destroyed (no CUDA calls at process exit).
+
+constexpr size_t kMaxCachedPlans = 64;
+
+template <typename K, typename P>
+struct PlanCache {
+    std::mutex m;
+    std::map<K, std::pair<std::shared_ptr<P>, unsigned long long>> map;
+    unsigned long long clock = 0;
+
+    std::shared_ptr<P> find(const K& k)
+    {
+        std::lock_guard<std::mutex> lk(m);
+        auto it = map.find(k);
+        if (it == map.end()) return nullptr;
+        it->second.second = ++clock;
+        return it->second.first;
+    }
+    // Adds p unless another thread added a plan for k first; returns the
+    // cached plan.  The plan dropped to make room is released after the lock.
+    std::shared_ptr<P> insert(const K& k, std::shared_ptr<P> p)
+    {
+        std::shared_ptr<P> dropped;
+        std::lock_guard<std::mutex> lk(m);
+        auto ins = map.emplace(k, std::make_pair(p, ++clock));
+        if (!ins.second) {
+            ins.first->second.second = clock;
+            return ins.first->second.first;
+        }
+        if (map.size() > kMaxCachedPlans) {
+            auto oldest = map.begin();
+            for (auto it = map.begin(); it != map.end(); ++it)
+                if (it->second.second < oldest->second.second) oldest = it;
+            dropped = std::move(oldest->second.first);
+            map.erase(oldest);
+        }
+        return p;
+    }
+    // Drops every plan for which f(plan) holds (outside the lock).
+    template <typename F>
+    void drop_if(F f)
+    {
+        std::vector<std::shared_ptr<P>> dropped;
+        {
+            std::lock_guard<std::mutex> lk(m);
+            for (auto it = map.begin(); it != map.end();) {
+                if (f(*it->second.first)) {
+                    dropped.push_back(std::move(it->second.first));
+                    it = map.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+    }
+    size_t size()
+    {
+        std::lock_guard<std::mutex> lk(m);
+        return map.size();
+    }
+};
+
 // ---- batched plans -------------------------------------------------------
 
 struct BatchKey {
@@ -576,27 +647,20 @@ struct BatchPlan {
     {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        if (dev_table || partial || counter) cudaDeviceSynchronize();   // replays in flight
         if (dev_table) cudaFree(dev_table);
         if (partial) cudaFree(partial);
         if (counter) cudaFree(counter);
     }
 };
 
-std::mutex g_batch_mutex;
-std::map<BatchKey, BatchPlan*> g_batches;
+PlanCache<BatchKey, BatchPlan>& g_batches = *new PlanCache<BatchKey, BatchPlan>;
 
 void drop_batches_using(const bude_deck* d)
 {
-    std::lock_guard<std::mutex> lk(g_batch_mutex);
-    for (auto it = g_batches.begin(); it != g_batches.end();) {
-        const auto& ds = it->second->decks;
-        if (std::find(ds.begin(), ds.end(), d) != ds.end()) {
-            delete it->second;
-            it = g_batches.erase(it);
-        } else {
-            ++it;
-        }
-    }
+    g_batches.drop_if([d](const BatchPlan& bp) {
+        return std::find(bp.decks.begin(), bp.decks.end(), d) != bp.decks.end();
+    });
 }
 
 }  // namespace
@@ -855,14 +919,9 @@ int bude_energies_batched(bude_deck* const* decks, const float* const* poses, co
         key.n.push_back(n[i]);
     }
     cudaStream_t s = (cudaStream_t)stream;
-    BatchPlan* bp = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_batch_mutex);
-        auto it = g_batches.find(key);
-        if (it != g_batches.end()) bp = it->second;
-    }
+    std::shared_ptr<BatchPlan> bp = g_batches.find(key);
     if (!bp) {
-        bp = new BatchPlan;
+        bp = std::make_shared<BatchPlan>();
         bp->r = r;
         std::vector<const bude_deck*> dv(decks, decks + count);
         std::vector<const float*> pv(poses, poses + count);
@@ -871,9 +930,9 @@ int bude_energies_batched(bude_deck* const* decks, const float* const* poses, co
         std::vector<float*> gv(count, nullptr);
         bp->decks = dv;
         rc = make_plan(dv, pv, nv, ov, gv, r, false, dev, &bp->pl);
-        if (rc) { delete bp; return rc; }
+        if (rc) return rc;
         const Plan& pl = bp->pl;
-        auto bail = [&](int code) { delete bp; return code; };
+        auto bail = [](int code) { return code; };   // bp frees what it holds
         if (!pl.inst.empty()) {
             cudaError_t e = dev_alloc((void**)&bp->dev_table, pl.inst.size() * sizeof(Instance));
             if (e) return bail(cuda_fail(e, "plan allocation"));
@@ -915,12 +974,7 @@ int bude_energies_batched(bude_deck* const* decks, const float* const* poses, co
         if (e) return bail(cuda_fail(e, "graph instantiation"));
         bp->launches = launches;
         // a plan another thread finished first for the same key wins; ours goes
-        std::lock_guard<std::mutex> lk(g_batch_mutex);
-        auto ins = g_batches.emplace(key, bp);
-        if (!ins.second) {
-            delete bp;
-            bp = ins.first->second;
-        }
+        bp = g_batches.insert(key, bp);
     }
     CK(cudaGraphLaunch(bp->exec, s), "graph launch");
     g_launches = bp->launches;
@@ -1034,8 +1088,15 @@ struct RefineKey {
     bool operator<(const RefineKey& o) const { return memcmp(this, &o, sizeof *this) < 0; }
 };
 
+// The plan owns every buffer its graph uses, the partial-sum workspace
+// included: the deck's own workspace is reallocated when a later call on the
+// deck needs more, and a captured graph would keep the freed address.
 struct RefinePlan {
     float* buf = nullptr;  // E[n] g[6n] trial[6n] Et[n] gt[6n] alpha[n]
+    double* partial = nullptr;
+    size_t partial_bytes = 0;
+    unsigned* counter = nullptr;
+    size_t counter_count = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const bude_deck* deck = nullptr;
@@ -1044,26 +1105,27 @@ struct RefinePlan {
     {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        if (buf || partial || counter) cudaDeviceSynchronize();   // replays in flight
         if (buf) cudaFree(buf);
+        if (partial) cudaFree(partial);
+        if (counter) cudaFree(counter);
     }
 };
 
-std::mutex g_refine_mutex;
-std::map<RefineKey, RefinePlan*> g_refines;
+PlanCache<RefineKey, RefinePlan>& g_refines = *new PlanCache<RefineKey, RefinePlan>;
 
 }  // namespace
 
 static void drop_refines_using(const bude_deck* d)
 {
-    std::lock_guard<std::mutex> lk(g_refine_mutex);
-    for (auto it = g_refines.begin(); it != g_refines.end();) {
-        if (it->second->deck == d) {
-            delete it->second;
-            it = g_refines.erase(it);
-        } else {
-            ++it;
-        }
-    }
+    g_refines.drop_if([d](const RefinePlan& rp) { return rp.deck == d; });
+}
+
+extern "C" BUDE_API int bude_debug_cached_plans(int32_t* batched, int32_t* refine)
+{
+    if (batched) *batched = (int32_t)g_batches.size();
+    if (refine) *refine = (int32_t)g_refines.size();
+    return BUDE_OK;
 }
 
 extern "C" BUDE_API int bude_refine(bude_deck* deck, float* poses, int64_t n, int32_t steps,
@@ -1101,16 +1163,11 @@ extern "C" BUDE_API int bude_refine(bude_deck* deck, float* poses, int64_t n, in
     key.n = n;
     key.steps = steps;
     key.step0 = step0;
-    RefinePlan* rp = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_refine_mutex);
-        auto it = g_refines.find(key);
-        if (it != g_refines.end()) rp = it->second;
-    }
+    std::shared_ptr<RefinePlan> rp = g_refines.find(key);
     if (!rp) {
-        rp = new RefinePlan;
+        rp = std::make_shared<RefinePlan>();
         rp->deck = deck;
-        auto bail = [&](int code) { delete rp; return code; };
+        auto bail = [](int code) { return code; };   // rp frees what it holds
         const size_t N = (size_t)n;
         cudaError_t e = dev_alloc((void**)&rp->buf, 22 * N * sizeof(float));
         if (e) return bail(cuda_fail(e, "refine buffers"));
@@ -1125,9 +1182,10 @@ extern "C" BUDE_API int bude_refine(bude_deck* deck, float* poses, int64_t n, in
         if (rc) return bail(rc);
         rc = make_plan({deck}, {trial}, {(long long)n}, {Et}, {gt}, r, true, dev, &p1);
         if (rc) return bail(rc);
-        rc = ensure_workspace(&deck->partial, &deck->partial_bytes, &deck->counter,
-                              &deck->counter_count, partial_bytes_for(p0, r, true),
-                              (size_t)p0.n_tiles, s);
+        rc = ensure_workspace(&rp->partial, &rp->partial_bytes, &rp->counter, &rp->counter_count,
+                              std::max(partial_bytes_for(p0, r, true),
+                                       partial_bytes_for(p1, r, true)),
+                              (size_t)std::max(p0.n_tiles, p1.n_tiles), s);
         if (rc) return bail(rc);
         e = cudaStreamSynchronize(s);
         if (e) return bail(cuda_fail(e, "refine synchronisation"));
@@ -1141,12 +1199,12 @@ extern "C" BUDE_API int bude_refine(bude_deck* deck, float* poses, int64_t n, in
         int lrc = BUDE_OK;
         cudaError_t ke = launch_refine_init(alpha, n, step0, cs);
         ++g_launches;
-        if (ke == cudaSuccess) lrc = launch_plan(p0, r, nullptr, deck->partial, deck->counter, cs);
+        if (ke == cudaSuccess) lrc = launch_plan(p0, r, nullptr, rp->partial, rp->counter, cs);
         for (int it = 0; it < steps && ke == cudaSuccess && lrc == BUDE_OK; ++it) {
             ke = launch_refine_propose(poses, g, alpha, trial, n, cs);
             ++g_launches;
             if (ke != cudaSuccess) break;
-            lrc = launch_plan(p1, r, nullptr, deck->partial, deck->counter, cs);
+            lrc = launch_plan(p1, r, nullptr, rp->partial, rp->counter, cs);
             if (lrc != BUDE_OK) break;
             ke = launch_refine_accept(poses, E, g, trial, Et, gt, alpha, n, kRefineGrow,
                                       kRefineShrink, cs);
@@ -1164,12 +1222,7 @@ extern "C" BUDE_API int bude_refine(bude_deck* deck, float* poses, int64_t n, in
         if (e) return bail(cuda_fail(e, "end capture"));
         e = cudaGraphInstantiate(&rp->exec, rp->graph, 0);
         if (e) return bail(cuda_fail(e, "graph instantiation"));
-        std::lock_guard<std::mutex> lk(g_refine_mutex);
-        auto ins = g_refines.emplace(key, rp);
-        if (!ins.second) {
-            delete rp;
-            rp = ins.first->second;
-        }
+        rp = g_refines.insert(key, rp);
     }
     CK(cudaGraphLaunch(rp->exec, s), "graph launch");
     g_launches = rp->launches;

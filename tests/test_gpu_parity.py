@@ -623,3 +623,21 @@ def test_device_named_without_index_is_the_current_device():
         deck = bude.Deck(D, device=dev)
         assert deck.device == torch.device(DEV)
         assert torch.equal(bude.energies(deck, P), ref)
+
+
+def test_batched_plan_cache_keeps_the_64_most_recent():
+    D = synth.make_deck(150, 8, 60, 34, 40)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    ref = bude.energies_batched([deck], [P])[0].clone()
+    outs = [torch.empty(P.shape[1], device=DEV) for _ in range(70)]
+    for o in outs:                                  # 70 argument sets: 70 plans built
+        bude.energies_batched([deck], [P], outs=[o])
+    assert bude.debug_cached_plans()[0] == 64
+    assert all(torch.equal(o, ref) for o in outs)
+    outs[0].zero_()                                 # dropped long ago: rebuilt
+    bude.energies_batched([deck], [P], outs=[outs[0]])
+    assert torch.equal(outs[0], ref)
+    assert bude.debug_cached_plans()[0] == 64
+    deck.close()                                    # every cached plan used this deck
+    assert bude.debug_cached_plans()[0] == 0

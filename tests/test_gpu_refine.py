@@ -121,3 +121,23 @@ def test_refine_replay_continues_and_zero_steps_scores():
         bude.refine_device(deck, P, steps=-1)
     with pytest.raises(bude.BudeError):
         bude.refine_device(deck, P, steps=2, step0=0.0)
+
+
+def test_refine_replay_after_the_deck_workspace_grows():
+    # the captured refinement graph owns its workspace: a later call on the
+    # deck that needs a larger one (the deck frees and reallocates its own)
+    # leaves the replay unchanged, and memory taken after it stays untouched
+    D = synth.make_deck(141, 16, 400, 34, 256)
+    deck = bude.Deck(D, device=DEV)
+    P0 = torch.from_numpy(D["poses"]).to(DEV)
+    P, E = P0.clone(), torch.empty(P0.shape[1], device=DEV)
+    bude.refine_device(deck, P, steps=4, step0=0.05, energies=E)       # captures
+    first_P, first_E = P.clone(), E.clone()
+    big = torch.from_numpy(synth.make_deck(142, 16, 400, 34, 200000)["poses"]).to(DEV)
+    bude.energies(deck, big, ppwi=1)           # 6250 pose tiles: the deck's workspace grows
+    fill = [torch.full((1 << 20,), 7.0, device=DEV) for _ in range(8)]
+    P.copy_(P0)
+    bude.refine_device(deck, P, steps=4, step0=0.05, energies=E)       # replays
+    torch.cuda.synchronize()
+    assert torch.equal(P, first_P) and torch.equal(E, first_E)
+    assert all(bool((f == 7.0).all()) for f in fill)

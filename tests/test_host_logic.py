@@ -214,6 +214,10 @@ def test_batched_outputs_are_checked_per_deck():
         bude.energies_batched(decks, poses, outs=[_meta(8), _meta(5, dtype=torch.float16)])
 
 
+def test_no_plans_are_cached_before_any_call():
+    assert bude.debug_cached_plans() == (0, 0)
+
+
 def test_stream_stencil_and_fock_refuse_bad_tensors_before_any_launch():
     # host tensors reach a kernel as host pointers; missing arrays as nulls
     import torch
