@@ -293,6 +293,26 @@ long long split_grid(const std::vector<Instance>& inst, long long u_total, long 
     return grid;
 }
 
+// Raise a kernel's limit on dynamic shared memory to at least `bytes`, never
+// lower it.  The limit belongs to the function (per device), not to a launch:
+// a lower value set for one call would fail a launch of another thread, or a
+// replay of a captured graph, that needs more.  The limit only permits; each
+// launch still asks for its own amount.
+cudaError_t raise_smem_limit(const void* fn, size_t bytes)
+{
+    static std::mutex m;
+    static auto& limits = *new std::map<std::pair<int, const void*>, size_t>;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(m);
+    size_t& cur = limits[{dev, fn}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 struct Plan {
     std::vector<Instance> inst;
     long long n_total = 0;
@@ -378,8 +398,7 @@ int make_plan(const std::vector<const bude_deck*>& decks, const std::vector<cons
     pl->smem = smem_max;
     pl->fn = kernel_for(r.variant, r.P, G, r.cull != 0);
     if (pl->inst.empty()) return BUDE_OK;
-    CK(cudaFuncSetAttribute(pl->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem),
-       "cudaFuncSetAttribute");
+    CK(raise_smem_limit(pl->fn, pl->smem), "shared-memory limit");
     int occ = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pl->fn, r.block, pl->smem),
        "occupancy query");
@@ -1272,8 +1291,7 @@ extern "C" BUDE_API int bude_param_grad(bude_deck* deck, const float* poses, int
     int chunk = (int)std::min<size_t>((size_t)deck->n_pro, (budget - fixed) / atom_bytes);
     if (r.tile > 0) chunk = std::min(chunk, r.tile);
     const size_t smem = param_smem_bytes(r.P, deck->n_lig, deck->n_rows, deck->n_types, chunk);
-    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-       "cudaFuncSetAttribute");
+    CK(raise_smem_limit(fn, smem), "shared-memory limit");
     int occ = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, r.block, smem), "occupancy query");
     if (occ < 1) return fail(BUDE_ERR_UNSUPPORTED, "block %d cannot be resident", r.block);

@@ -641,3 +641,22 @@ def test_batched_plan_cache_keeps_the_64_most_recent():
     assert bude.debug_cached_plans()[0] == 64
     deck.close()                                    # every cached plan used this deck
     assert bude.debug_cached_plans()[0] == 0
+
+
+def test_batched_replay_after_a_smaller_launch_of_the_same_kernel():
+    # a kernel's shared-memory limit only grows: a plain launch of the same
+    # kernel on a small deck, between two replays of a batch that needs far
+    # more shared memory, leaves the replay valid and unchanged
+    big = synth.make_deck(160, 32, 5000, 34, 512)
+    small = synth.make_deck(161, 4, 40, 34, 64)
+    db, ds = bude.Deck(big, device=DEV), bude.Deck(small, device=DEV)
+    Pb = torch.from_numpy(big["poses"]).to(DEV)
+    Ps = torch.from_numpy(small["poses"]).to(DEV)
+    opts = bude.LaunchOptions(variant="ieee", ppwi=8, block=256)
+    out = bude.energies_batched([db], [Pb], opts=opts)[0]
+    first = out.clone()
+    bude.energies(ds, Ps, opts=opts)
+    out.zero_()
+    bude.energies_batched([db], [Pb], outs=[out], opts=opts)
+    torch.cuda.synchronize()
+    assert torch.equal(out, first)
