@@ -169,6 +169,18 @@ __device__ __forceinline__ double erf_over_x(double x2)
     const double r = rsqrt(y);
     return erf(y * r) * r;
 }
+// 1/sqrt(x) for a positive normal float by the approximate reciprocal root
+// with subnormals flushed: every argument here (1/p + 1/q of primitive
+// exponents, or t >= 32) is a normal number, where this is the same MUFU
+// operation as rsqrtf without the scaling rsqrtf wraps around it for
+// subnormal inputs.
+__device__ __forceinline__ float rsqrt_normal(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // erf(x)/x from x^2 = t by the table above (tab in shared memory): round 16 t
 // to the nearest grid index with the 1.5 2^23 shift, so that the index is in
 // the low mantissa bits and the grid point is exact, then three FMAs.
@@ -181,7 +193,7 @@ __device__ __forceinline__ float erf_over_x(float t, const float4* __restrict__ 
     const float d = fmaf(y - kShift, -1.f / kBoysPerUnit, tc);
     const float4 c = tab[i];
     const float f = fmaf(fmaf(fmaf(c.w, d, c.z), d, c.y), d, c.x);
-    return t < (float)kBoysTmax ? f : rsqrtf(t);
+    return t < (float)kBoysTmax ? f : rsqrt_normal(t);
 }
 // The same in FP64 with the finer table (read through the L1 cache: 55 KB),
 // the 1.5 2^52 shift and five FMAs.
@@ -203,7 +215,7 @@ __device__ __forceinline__ double erf_over_x(double t, const double2* __restrict
 
 // Precision-matched helpers for the template below (declared before it, so
 // that the float instantiation never promotes to double).
-__device__ __forceinline__ float hf_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float hf_rsqrt(float x) { return rsqrt_normal(x); }
 __device__ __forceinline__ double hf_rsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float hf_fma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double hf_fma(double a, double b, double c) { return fma(a, b, c); }
