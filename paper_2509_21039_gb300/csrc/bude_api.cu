@@ -172,8 +172,11 @@ size_t record_bytes(int variant, bool G, int P)
     return G ? sizeof(PairG) : sizeof(PairF);
 }
 
-// Bytes of one staged protein atom in shared memory.
-size_t protein_bytes(int variant, int P, bool G) { return packed(variant, P, G) ? 32 : 16; }
+// Bytes of one staged protein atom in shared memory (mirrors PRO4).
+size_t protein_bytes(int variant, int P, bool G)
+{
+    return (packed(variant, P, G) || variant == BUDE_FP64) ? 32 : 16;
+}
 
 // Per-chunk run table and ligand-row cost prefix of the packed kernels.
 size_t run_bytes(int variant, int P, bool G, int n_types, int n_lig)
