@@ -88,9 +88,11 @@ __global__ void build_tables_kernel(const float4* __restrict__ lig_src, int n_li
         const double w = ((ha == 1 && hb == 2) || (ha == 2 && hb == 1)) ? 2.0 : 1.0;
         const double cE = kKE * (double)fa.z * (double)fb.z * w;
         const double S = ((ha != 0) != (hb != 0)) ? kKD : 0.0;
+        const double inv_r = 1.0 / R;
+        const double sh = sqrt(fabs(H));
         PairD d;
-        d.inv_r = 1.0 / R;
-        d.h = H;
+        d.sa = sh / R;
+        d.sb = copysign(sh, H);
         d.ce = R / kDE + 1.0;
         d.ke1 = -2.0 * cE;
         d.ke0 = 3.0 * cE;
@@ -99,19 +101,18 @@ __global__ void build_tables_kernel(const float4* __restrict__ lig_src, int n_li
         d.kd0 = 3.0 * S;
         tabD[i] = d;
         PairF f;
-        f.inv_r = (float)d.inv_r; f.h = (float)d.h; f.ce = (float)d.ce; f.ke1 = (float)d.ke1;
+        f.inv_r = (float)inv_r; f.h = (float)H; f.ce = (float)d.ce; f.ke1 = (float)d.ke1;
         f.ke0 = (float)d.ke0; f.cd = (float)d.cd; f.kd1 = (float)d.kd1; f.kd0 = (float)d.kd0;
         tabF[i] = f;
         PairG g;
         g.inv_r = f.inv_r; g.h = f.h; g.ce = f.ce; g.ke1 = f.ke1;
         g.ke0 = f.ke0; g.cd = f.cd; g.kd1 = f.kd1; g.kd0 = f.kd0;
-        g.hs = (float)(-2.0 * H * d.inv_r);
+        g.hs = (float)(-2.0 * H * inv_r);
         g.ae1 = (float)(-3.0 / kDE * d.ke1);
         g.ae0 = (float)(-2.0 / kDE * d.ke0);
         g.ad1 = (float)(-3.0 / kDD * d.kd1);
         g.ad0 = (float)(-2.0 / kDD * d.kd0);
-        const double sh = sqrt(fabs(H));
-        g.sa = (float)(sh * d.inv_r);
+        g.sa = (float)(sh * inv_r);
         g.sb = (float)sh;
         g.pad = 0.f;
         tabG[i] = g;
