@@ -58,7 +58,7 @@ extern "C" {
 #define BUDE_FP32_COMP 2 /* as IEEE, each ligand atom's FP32 sum folded in FP64 */
 #define BUDE_FP64 3      /* every operation in FP64 */
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define BUDE_MAX_TYPES 1024
 
 /*
