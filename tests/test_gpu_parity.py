@@ -89,6 +89,22 @@ def test_protein_chunking_and_grid(tile, cps):
     check(D, "ieee", ppwi=4, block=128, tile=tile, ctas_per_sm=cps)
 
 
+@pytest.mark.parametrize("tile", [32, 257])
+@pytest.mark.parametrize("variant,ppwi", [("fast", 16), ("fp64", 4), ("fp64", 1)])
+def test_protein_chunking_other_layouts(tile, variant, ppwi):
+    # the packed kernels stage each protein atom as two duplicated float4
+    # pairs and the FP64 kernel as two double pairs; chunks that cut the
+    # type runs exercise both layouts, for energies and pose gradients
+    D = synth.make_deck(105, 11, 700, 34, 640)
+    _, ref, A = check(D, variant, ppwi=ppwi, block=128, tile=tile)
+    Eref, Gref, S = oracle.pose_grad(D, D["poses"], n_threads=-1, with_scale=True)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    E, G = bude.pose_grad(deck, P, variant=variant, ppwi=min(ppwi, 8), block=128, tile=tile)
+    assert scaled_error(E.cpu().numpy(), Eref, A, variant).max() <= GATE[variant]
+    assert grad_error(G.cpu().numpy(), Gref, S, variant) <= GRAD_GATE[variant]
+
+
 def test_small_config_seed0_every_variant():
     D = synth.make_deck(0, **synth.SMALL)
     ref, A = oracle.energies(D, D["poses"], n_threads=-1, with_abs=True)
