@@ -339,3 +339,28 @@ def test_work_split_of_the_batched_workload():
     nt = [-(-n // 512) for _, _, n in shapes]
     w = [100 + (17 * i) % 40 for i in range(64)]
     assert _check_partition(K, nt, w, 152, with_owner=False) == 152
+
+
+def test_reference_arm_line_and_other_ranks(tmp_path):
+    # the reference arm times the oracle on the host: one JSON line on rank 0
+    # with the keys the bench contract names; any other rank prints nothing
+    import json
+    import subprocess
+    import sys
+    env = dict(os.environ, RANK="0")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "1"], capture_output=True, text=True,
+                         env=env, cwd=ROOT, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["unit"] == "poses/s" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["higher_is_better"] is True
+    assert line["config"]["workload"].startswith("deck 64 lig x 2672 pro x 65536 poses")
+    env["RANK"] = "1"
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "1"], capture_output=True, text=True,
+                         env=env, cwd=ROOT, timeout=600)
+    assert out.returncode == 0 and out.stdout.strip() == ""
