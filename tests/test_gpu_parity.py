@@ -678,3 +678,32 @@ def test_batched_replay_after_a_smaller_launch_of_the_same_kernel():
     bude.energies_batched([db], [Pb], outs=[out], opts=opts)
     torch.cuda.synchronize()
     assert torch.equal(out, first)
+
+
+def test_launch_counts_of_each_call():
+    # bude_last_launch_count reports the kernels a call enqueued (the bench's
+    # gpu_launches adds these up): one persistent launch per energy, gradient
+    # or batched call, 2 + 3 x steps for a refinement, none for a deck with
+    # no atom pairs (its outputs are cleared by a memset)
+    D = synth.make_deck(180, 6, 90, 34, 300)
+    deck = bude.Deck(D, device=DEV)
+    P = torch.from_numpy(D["poses"]).to(DEV)
+    bude.energies(deck, P)
+    assert bude.launch_count() == 1
+    bude.energies_noalloc(deck, P, torch.empty(P.shape[1], device=DEV))
+    assert bude.launch_count() == 1
+    bude.pose_grad(deck, P)
+    assert bude.launch_count() == 1
+    D2 = synth.make_deck(181, 9, 120, 34, 77)
+    deck2 = bude.Deck(D2, device=DEV)
+    P2 = torch.from_numpy(D2["poses"]).to(DEV)
+    for _ in range(2):                               # first call captures, second replays
+        bude.energies_batched([deck, deck2], [P, P2])
+        assert bude.launch_count() == 1
+    for _ in range(2):
+        bude.refine_device(deck, P.clone(), steps=3, step0=0.05)
+        assert bude.launch_count() == 2 + 3 * 3
+    empty = dict(D, lig_xyz=D["lig_xyz"][:0], lig_type=D["lig_type"][:0])
+    E = bude.energies(bude.Deck(empty, device=DEV), P)
+    assert bude.launch_count() == 0 and not E.any()
+    torch.cuda.synchronize()
