@@ -65,6 +65,15 @@ MEASURED_EXECUTED_PARAM = {"kernel_sha256_16": "836eeb0553732cf7", "variant": "f
                            "flop_per_pair": 39.12}
 
 
+# FP64-pipe thread instructions per pose-pair of the FP64 energy kernel (DFMA,
+# DMUL, DADD and the conversions that share the pipe), from ncu's
+# smsp__inst_executed_pipe_fp64 of one launch on the full deck's first 4096
+# poses, for the kernel source with this hash.  GB300's nominal FP64 rate of
+# 1.25 TFLOP/s is 6.25e11 such instructions per second.
+MEASURED_FP64_PIPE = {"kernel_sha256_16": "bbb752c7b8eccbe4", "ppwi": 4, "ops_per_pair": 19.88}
+NOMINAL_FP64_INST_PER_S = 6.25e11
+
+
 def kernel_sha(files=("bude_kernels.cuh",)):
     """First 16 hex digits of the sha256 of the kernel sources (csrc/) with
     comments and whitespace removed, so that edits to comments keep the
@@ -124,6 +133,37 @@ def traffic_source(variant, ppwi, block, n_poses):
         return (f"null: DRAM bytes were captured for {m['variant']} P={m['ppwi']} "
                 f"block={m['block']} on {FULL['n_poses']} poses")
     return f"ncu dram__bytes_read.sum + dram__bytes_write.sum of kernel source {sha}"
+
+
+def fp64_pipe_fraction(ppwi, pairs_per_s):
+    """(FP64-pipe instructions per second, fraction of the nominal FP64 rate)
+    of the FP64 energy kernel, or (None, None) when the counts do not belong
+    to this kernel source and shape."""
+    m = MEASURED_FP64_PIPE
+    if m["ops_per_pair"] is None or (kernel_sha(), ppwi) != (m["kernel_sha256_16"], m["ppwi"]):
+        return None, None
+    ips = m["ops_per_pair"] * pairs_per_s
+    return ips, ips / NOMINAL_FP64_INST_PER_S
+
+
+def fp64_throughput(bude, synth, dev, timed):
+    """The FP64 variant on the full deck's first 4096 poses (it runs about 80x
+    slower than FAST on GB300, whose FP64 units are a small fraction of its
+    FP32 ones), in the library's default (tuned) shape."""
+    import torch
+    D = synth.make_deck(1, **FULL)
+    deck = bude.Deck(D, device=dev)
+    P = torch.from_numpy(D["poses"][:, :4096].copy()).to(dev)
+    out = torch.empty(P.shape[1], dtype=torch.float32, device=dev)
+    o = bude.default_options("fp64")
+    ms, _ = timed(lambda: bude.energies(deck, P, out=out, opts=o), 3, 1)
+    deck.close()
+    t = statistics.mean(ms) / 1e3
+    ips, frac = fp64_pipe_fraction(o.ppwi, FULL["n_lig"] * FULL["n_pro"] * P.shape[1] / t)
+    return {"workload": "64 lig x 2672 pro, first 4096 of the 65536 poses, seed 1",
+            "ms": t * 1e3, "poses_per_s": P.shape[1] / t,
+            "opts": {"ppwi": o.ppwi, "block": o.block, "ctas_per_sm": o.ctas_per_sm},
+            "fp64_pipe_instructions_per_s": ips, "frac_of_nominal_fp64_rate": frac}
 
 
 def eq3_flops(n_lig, n_pro, n_poses, ppwi):
@@ -723,6 +763,8 @@ def main():
                     help="only the forcefield-gradient extra (profiling)")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the pose-gradient (adjoint) extra (profiling)")
+    ap.add_argument("--fp64-only", action="store_true",
+                    help="only the FP64 variant on the full deck's first 4096 poses (profiling)")
     ap.add_argument("--hf-only", type=int, default=0, metavar="ATOMS",
                     help="only the Fock build on this many atoms (profiling)")
     ap.add_argument("--hf-variant", default="ieee", choices=["ieee", "fp64"],
@@ -845,6 +887,12 @@ def main():
         res = adjoint_throughput(bude, synth, tune, dev, timed, variant=args.variant)
         if rank == 0:
             print(json.dumps({"adjoint": res}), flush=True)
+        return
+
+    if args.fp64_only:
+        res = fp64_throughput(bude, synth, dev, timed)
+        if rank == 0:
+            print(json.dumps({"fp64": res}), flush=True)
         return
 
     if args.hf_only:
@@ -1025,6 +1073,13 @@ def main():
                                    "rel_err_max": float(rel.max()),
                                    "error_sample_poses": int(len(rf)),
                                    "timed_poses": int(npos)}
+                if vname == "fp64":
+                    ips, frac = fp64_pipe_fraction(o.ppwi if o.ppwi else
+                                                   bude.default_options("fp64").ppwi,
+                                                   shape["n_lig"] * shape["n_pro"] * npos / t)
+                    if frac is not None:
+                        variants[vname]["fp64_pipe_instructions_per_s"] = ips
+                        variants[vname]["frac_of_nominal_fp64_rate"] = frac
                 xv = measured_executed(vname)
                 if xv is not None:
                     variants[vname]["executed_frac"] = (xv * shape["n_lig"] * shape["n_pro"] * npos
