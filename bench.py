@@ -670,6 +670,8 @@ def summary(line):
     for v, row in line.get("variants", {}).items():
         out[v] = {"poses_s": _r(row["poses_per_s"]), "eq3_frac": _r(row["frac_fp32_peak"]),
                   "err": _r(row["scaled_err_max"], 2)}
+        if row.get("frac_of_nominal_fp64_rate") is not None:
+            out[v]["fp64_rate_frac"] = _r(row["frac_of_nominal_fp64_rate"])
     b = line.get("batched")
     if b:
         out["batched"] = {"ms": _r(b["batched_ms"]), "plain_ms": _r(b["plain_ms"]),
