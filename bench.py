@@ -73,6 +73,12 @@ MEASURED_EXECUTED_PARAM = {"kernel_sha256_16": "836eeb0553732cf7", "variant": "f
 MEASURED_FP64_PIPE = {"kernel_sha256_16": "bbb752c7b8eccbe4", "ppwi": 4, "ops_per_pair": 19.88}
 NOMINAL_FP64_INST_PER_S = 6.25e11
 
+# The same count for the all-FP64 Fock build, per primitive integral, on the
+# 128-atom lattice (3 primitives per atom) where it was taken: the share of
+# primitives past the erf table's end, which take a reciprocal root instead,
+# depends on the lattice, so the count is used for that size only.
+MEASURED_HF64_PIPE = {"kernel_sha256_16": "89ff5a2f775cd570", "atoms": 128, "ops_per_primitive": 30.47}
+
 
 def kernel_sha(files=("bude_kernels.cuh",)):
     """First 16 hex digits of the sha256 of the kernel sources (csrc/) with
@@ -586,6 +592,11 @@ def hartree_fock(bude, synth, dev, timed, sizes=(64, 128, 256), variants=("ieee"
         row["quartets"] = q
         row["fp32_primitive_integrals_per_s"] = q * 81 / (row["fp32_integrals_ms"] / 1e3)
         row["fp64_primitive_integrals_per_s"] = q * 81 / (row["fp64_ms"] / 1e3)
+        m = MEASURED_HF64_PIPE
+        if (kernel_sha(("bude_hf.cu",)), n) == (m["kernel_sha256_16"], m["atoms"]):
+            ips = m["ops_per_primitive"] * row["fp64_primitive_integrals_per_s"]
+            row["fp64_pipe_instructions_per_s"] = ips
+            row["fp64_frac_of_nominal_fp64_rate"] = ips / NOMINAL_FP64_INST_PER_S
         out[f"a={n} ngauss=3"] = row
         hf.close()
     return out
