@@ -315,6 +315,86 @@ __device__ __forceinline__ T contracted_ranked(const T4* __restrict__ pq, const 
     return v;
 }
 
+// The FP32 form of contracted_ranked for G2 >= 2 on packed FP32x2
+// instructions (Blackwell's FADD2/FMUL2/FFMA2): the partner's primitive pairs
+// go in twos, so one instruction serves two primitive integrals wherever
+// their operands pair up (distances, exponent sums, t, the grid offsets and
+// the prefactors); the table reads, the Horner steps and the roots stay
+// scalar.  The partner's coordinates are kept negated, so that x - c is one
+// packed add with the same rounding.  Half the issue slots of the scalar
+// loop's FP32 work; the two lanes' sums of each ab meet once at its end.
+template <int G2>
+__device__ __forceinline__ float contracted_ranked_x2(const float4* __restrict__ pq,
+                                                      const float* __restrict__ kp, long long m,
+                                                      long long a, long long b,
+                                                      const float4* __restrict__ tab)
+{
+    constexpr int NP = G2 / 2;
+    constexpr float kShift = 12582912.f;   // 1.5 * 2^23, as in erf_over_x
+    float2 ncx[NP], ncy[NP], ncz[NP], cw[NP], ck[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const float4 u = pq[(2 * k) * m + b], v = pq[(2 * k + 1) * m + b];
+        ncx[k] = make_float2(-u.x, -v.x);
+        ncy[k] = make_float2(-u.y, -v.y);
+        ncz[k] = make_float2(-u.z, -v.z);
+        cw[k] = make_float2(u.w, v.w);
+        ck[k] = make_float2(kp[(2 * k) * m + b], kp[(2 * k + 1) * m + b]);
+    }
+    float4 cl = make_float4(0.f, 0.f, 0.f, 0.f);
+    float kl = 0.f;
+    if constexpr (G2 % 2) {
+        cl = pq[(G2 - 1) * m + b];
+        kl = kp[(G2 - 1) * m + b];
+    }
+    const float2 shift2 = make_float2(kShift, kShift);
+    const float2 per2 = make_float2((float)kBoysPerUnit, (float)kBoysPerUnit);
+    const float2 inv2 = make_float2(-1.f / kBoysPerUnit, -1.f / kBoysPerUnit);
+    float v = 0.f;
+    // rolled over ab, as in contracted_ranked (instruction cache)
+#pragma unroll 1
+    for (int ab = 0; ab < G2; ++ab) {
+        const float4 x = pq[ab * m + a];
+        const float ka = kp[ab * m + a];
+        const float2 xx = make_float2(x.x, x.x), xy = make_float2(x.y, x.y);
+        const float2 xz = make_float2(x.z, x.z), xw = make_float2(x.w, x.w);
+        float2 w2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const float2 dx = __fadd2_rn(xx, ncx[k]);
+            const float2 dy = __fadd2_rn(xy, ncy[k]);
+            const float2 dz = __fadd2_rn(xz, ncz[k]);
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            const float2 sw = __fadd2_rn(xw, cw[k]);
+            const float2 rs = make_float2(rsqrt_normal(sw.x), rsqrt_normal(sw.y));   // sqrt(rho)
+            const float2 t = __fmul2_rn(__fmul2_rn(r2, rs), rs);
+            // erf(x)/x of both, as erf_over_x: grid index and offset packed
+            const float2 tc = make_float2(fminf(t.x, (float)kBoysTmax), fminf(t.y, (float)kBoysTmax));
+            const float2 y = __ffma2_rn(tc, per2, shift2);
+            const float2 d = __ffma2_rn(__fadd2_rn(y, make_float2(-kShift, -kShift)), inv2, tc);
+            const float4 c0 = tab[__float_as_int(y.x) - __float_as_int(kShift)];
+            const float4 c1 = tab[__float_as_int(y.y) - __float_as_int(kShift)];
+            float2 f;
+            f.x = fmaf(fmaf(fmaf(c0.w, d.x, c0.z), d.x, c0.y), d.x, c0.x);
+            f.y = fmaf(fmaf(fmaf(c1.w, d.y, c1.z), d.y, c1.y), d.y, c1.x);
+            f.x = t.x < (float)kBoysTmax ? f.x : rsqrt_normal(t.x);
+            f.y = t.y < (float)kBoysTmax ? f.y : rsqrt_normal(t.y);
+            w2 = __ffma2_rn(__fmul2_rn(ck[k], rs), f, w2);
+        }
+        float w = w2.x + w2.y;
+        if constexpr (G2 % 2) {
+            const float dx = x.x - cl.x, dy = x.y - cl.y, dz = x.z - cl.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float rs = rsqrt_normal(x.w + cl.w);
+            w = fmaf(kl * rs, erf_over_x(r2 * rs * rs, tab, 0u), w);
+        }
+        v = fmaf(ka, w, v);
+    }
+    return v;
+}
+
 // Gather of the primitive products into the rank-ordered copies.
 __global__ void hf_rank_copy_kernel(const HfPlanDev P, double4_32a* __restrict__ rpq,
                                     double* __restrict__ rkp, float4* __restrict__ rpqf,
@@ -460,9 +540,13 @@ __global__ void __launch_bounds__(128, 1) hf_fock_kernel(const HfPlanDev P,
         const long long b = x - prefix[a];
         const int2 pij = P.rpairs[a], pkl = P.rpairs[b];
         const int i = pij.x, j = pij.y, k = pkl.x, l = pkl.y;
-        double v = F32 ? (double)contracted_ranked<float, float4, G2>(P.rpqf, P.rkpf, P.m, a, b, g2, tab)
-                       : contracted_ranked<double, double4_32a, G2>(P.rpq, P.rkp, P.m, a, b, g2,
-                                                                    P.boys64);
+        double v;
+        if constexpr (F32 && G2 >= 2)
+            v = (double)contracted_ranked_x2<G2>(P.rpqf, P.rkpf, P.m, a, b, tab);
+        else if constexpr (F32)
+            v = (double)contracted_ranked<float, float4, G2>(P.rpqf, P.rkpf, P.m, a, b, g2, tab);
+        else
+            v = contracted_ranked<double, double4_32a, G2>(P.rpq, P.rkp, P.m, a, b, g2, P.boys64);
         if (i == j) v *= 0.5;
         if (k == l) v *= 0.5;
         if (a == b) v *= 0.5;
