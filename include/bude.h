@@ -114,7 +114,6 @@ typedef struct {
  */
 
 typedef struct bude_deck bude_deck;
-typedef struct bude_batch bude_batch;
 
 /*
  * bude_create_deck -- validate and repack one deck into buffers it owns.
