@@ -191,6 +191,19 @@ def measured_peaks():
         return {}
 
 
+def smi_id(local):
+    """nvidia-smi's name for CUDA device `local`: its UUID, which stays right
+    when CUDA_VISIBLE_DEVICES renumbers the devices; the index otherwise."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    return str(local)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -924,7 +937,7 @@ def main():
             print(json.dumps({"hbm_calibration": res}), flush=True)
         return
 
-    with ClockSampler(local, args.clocks_csv) as clk:
+    with ClockSampler(smi_id(local), args.clocks_csv) as clk:
         ms, launches = timed(step, args.steps, args.warmup)
     ms_mean = bdist.max_over_ranks(statistics.mean(ms), dev)
     value = total_units / (ms_mean / 1e3)
