@@ -789,6 +789,8 @@ def main():
                     help="only the forcefield-gradient extra (profiling)")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the pose-gradient (adjoint) extra (profiling)")
+    ap.add_argument("--refine-only", action="store_true",
+                    help="only the refinement extra (profiling)")
     ap.add_argument("--fp64-only", action="store_true",
                     help="only the FP64 variant on the full deck's first 4096 poses (profiling)")
     ap.add_argument("--hf-only", type=int, default=0, metavar="ATOMS",
@@ -913,6 +915,12 @@ def main():
         res = adjoint_throughput(bude, synth, tune, dev, timed, variant=args.variant)
         if rank == 0:
             print(json.dumps({"adjoint": res}), flush=True)
+        return
+
+    if args.refine_only:
+        res = refine_throughput(bude, synth, tune, dev, timed, variant=args.variant)
+        if rank == 0:
+            print(json.dumps({"refine": res}), flush=True)
         return
 
     if args.fp64_only:
